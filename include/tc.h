@@ -1,0 +1,214 @@
+/*
+ * tc.h -- C ABI of the GB300 exact triangle counter.
+ *
+ * The library counts the triangles of a simple undirected graph exactly, by
+ * the method of Tom and Karypis, "A 2D Parallel Triangle Counting Algorithm
+ * for Distributed-Memory Architectures" (ICPP 2019):
+ *
+ *   - the graph is made simple and undirected (Section 2, Section 6.1),
+ *   - vertices are relabelled in non-decreasing degree (Section 3.1,
+ *     Section 5.3 "Reorder vertices based on non-decreasing degree"),
+ *   - each edge is kept once, in the upper triangular part U (Section 5.3
+ *     "Create the upper and the lower triangular portion"), rows sorted,
+ *   - every edge (i,j) of U contributes c_ij = sum_{k>j} u_ik u_jk (Eq. 1),
+ *     the total being the sum of c_ij over U (Eq. 2); equivalently the
+ *     entries of UL at the nonzeros of U (Eq. 6, Eq. 7), summed.
+ *
+ * Counting follows the paper's <j,i,k> map-based enumeration (Section 3.1,
+ * Section 5.1 last paragraph): for each vertex j the row U_j is hashed once
+ * and probed by the part after j of every row U_i with i in column j.
+ *
+ * All entry points return a tc_status and never abort or throw.  On failure
+ * tc_last_error() gives a message (per host thread) and no output is written.
+ * All device pointers are CUDA device (or managed) memory of the current
+ * device; `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Entry points that must read a size back from the device
+ * synchronise the stream; each says so.
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TC_API __attribute__((visibility("default")))
+#else
+#define TC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TC_OK = 0,
+    TC_EINVAL = 1,     /* bad argument: NULL pointer, negative size, id outside [0,n) */
+    TC_ENOMEM = 2,     /* device allocation failed (including an injected failure) */
+    TC_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+    TC_ETIMEOUT = 4,   /* a bounded device wait ran out (serving queue) */
+    TC_EBUSY = 5,      /* over the admission budget (serving) */
+    TC_EUNSUPPORTED = 6
+} tc_status;
+
+/* Opaque preprocessed graph.  Owns one device arena (the single-blob layout
+ * of Section 5.2, last paragraph) holding the degree-ordered U in CSR, the
+ * <j,i,k> task lists, the work units and the relabelling. */
+typedef struct tc_graph tc_graph;
+
+/* Caller-supplied device allocator; NULL selects cudaMallocAsync on the
+ * call's stream.  alloc returns NULL on failure.  free receives the size
+ * that was allocated. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* ctx, void* stream);
+    void (*free)(void* ptr, size_t bytes, void* ctx, void* stream);
+    void* ctx;
+} tc_allocator;
+
+/* tc_preprocess flags */
+#define TC_INPUT_ON_DEVICE 0x1u  /* src/dst are device pointers (else host) */
+#define TC_OFFSETS_32      0x2u  /* force 32-bit CSR offsets (EINVAL if m >= 2^31) */
+#define TC_OFFSETS_64      0x4u  /* force 64-bit CSR offsets */
+/* With neither offset flag, 32-bit offsets are used when m < 2^31. */
+
+/* Counting knobs.  Zero in any field selects its default.  The count never
+ * depends on them; only speed does. */
+typedef struct {
+    int32_t small_max_outdeg;  /* pivots with |U_j| <= this go to warp units (<= 64) */
+    int32_t warp_unit_tasks;   /* tasks per warp unit */
+    int32_t cta_unit_tasks;    /* tasks per CTA unit */
+    int32_t cta_threads;       /* threads per CTA of the large-pivot kernel (128..1024) */
+    int32_t slice_max;         /* pivot entries hashed at once by one CTA (<= 8192) */
+    int32_t reserved[3];
+} tc_tuning;
+
+/* Graph facts, computed during preprocessing. */
+typedef struct {
+    int64_t n;              /* vertices */
+    int64_t num_pairs;      /* input pairs */
+    int64_t m;              /* simple undirected edges = nnz(U) */
+    int64_t max_deg;        /* max d(v) */
+    int64_t max_outdeg;     /* max |U_v| */
+    int64_t tasks;          /* edges (i,j) of U with a nonempty part of U_i after j */
+    uint64_t probes;        /* sum over tasks of |{k in U_i : k > j}| = sum_i C(|U_i|,2) */
+    int64_t small_units;    /* work units of the warp kernel */
+    int64_t large_units;    /* work units of the CTA kernel */
+    int64_t device_bytes;   /* bytes held by the graph's arena */
+    int32_t offset_bytes;   /* 4 or 8 */
+    int32_t pad;
+} tc_graph_stats;
+
+/*
+ * tc_preprocess -- Section 5.3 on one device: simple-graph conversion, degree
+ * counting, relabelling in non-decreasing (degree, id) order, orientation into
+ * U, CSR build with sorted rows, the <j,i,k> task lists (Section 5.1, last
+ * paragraph) and degree-binned work units (the doubly sparse list of
+ * Section 5.2 becomes the unit list: empty rows get no unit).
+ *
+ *   src, dst   num_pairs vertex ids each (int32, in [0, n)); pair e is the
+ *              undirected edge {src[e], dst[e]}.  Self-loops are dropped and
+ *              duplicates (either direction) merged.  Host pointers unless
+ *              flags has TC_INPUT_ON_DEVICE.  Read only; the caller keeps
+ *              ownership and may free them once the call returns.
+ *   num_pairs  >= 0.          n  number of vertices, 0 <= n < 2^31.
+ *   flags      TC_INPUT_ON_DEVICE, TC_OFFSETS_32, TC_OFFSETS_64.
+ *   alloc      device allocator, or NULL for cudaMallocAsync.
+ *   stream     cudaStream_t as void*.  The call synchronises it.
+ *   out        receives the new graph (owned by the caller until
+ *              tc_graph_free); untouched on failure.
+ *
+ * Errors: TC_EINVAL for NULL src/dst with num_pairs > 0, NULL out, negative
+ * sizes, n >= 2^31, or any id outside [0, n); TC_ENOMEM; TC_ECUDA.
+ */
+TC_API tc_status tc_preprocess(const int32_t* src, const int32_t* dst, int64_t num_pairs,
+                        int64_t n, uint32_t flags, const tc_allocator* alloc,
+                        void* stream, tc_graph** out);
+
+/*
+ * tc_count -- Eq. 1 and Eq. 2 over the graph: the exact number of triangles,
+ * and optionally the number of triangles through each vertex.
+ *
+ *   g            a graph from tc_preprocess (not modified; one count at a
+ *                time per graph, since the work queues live in its arena).
+ *   tune         NULL for defaults.
+ *   total_host   if non-NULL, receives the total; the call then synchronises
+ *                the stream.
+ *   total_dev    if non-NULL, device uint64 that receives the total
+ *                (stream ordered, no synchronisation needed).
+ *   per_vertex_dev  NULL, or device array of n uint64 that receives, for each
+ *                ORIGINAL vertex id v, the triangles containing v
+ *                (overwritten; their sum is 3 x total).
+ *   stream       cudaStream_t as void*.
+ *
+ * Errors: TC_EINVAL for NULL g, or both totals NULL and per_vertex_dev NULL;
+ * TC_ECUDA.
+ */
+TC_API tc_status tc_count(const tc_graph* g, const tc_tuning* tune, uint64_t* total_host,
+                   uint64_t* total_dev, uint64_t* per_vertex_dev, void* stream);
+
+/*
+ * tc_triangles -- one call from host pair lists to host results: H2D copy,
+ * tc_preprocess, tc_count, D2H copy, release.  Same arguments and errors as
+ * the two calls it makes; total_host must be non-NULL, per_vertex_host is
+ * NULL or n host uint64.  Synchronises the stream.
+ */
+TC_API tc_status tc_triangles(const int32_t* src_host, const int32_t* dst_host, int64_t num_pairs,
+                       int64_t n, uint32_t flags, void* stream, uint64_t* total_host,
+                       uint64_t* per_vertex_host);
+
+/* Fills *out with the graph's facts.  TC_EINVAL on NULL arguments. */
+TC_API tc_status tc_graph_get_stats(const tc_graph* g, tc_graph_stats* out);
+
+/* Releases the graph's arena on the stream given at preprocessing.
+ * NULL is accepted and ignored. */
+TC_API void tc_graph_free(tc_graph* g);
+
+/* Defaults for every tc_tuning field.  TC_EINVAL on NULL. */
+TC_API tc_status tc_tuning_default(tc_tuning* out);
+
+/* Last error message of the calling host thread ("" if none). */
+TC_API const char* tc_last_error(void);
+
+/*
+ * tc_generate_rmat -- device copy of the seeded RMAT input generator (not
+ * part of the paper's method; it produces synthetic inputs on the device so
+ * that large workloads need no host generation or upload).  Writes pairs
+ * [e0, e0+count) of the stream of (seed, scale, n) to src_dev / dst_dev
+ * (device int32, count entries each).  t1 < t2 < t3 are the cumulative a,
+ * a+b, a+b+c probabilities scaled to 2^32.  The stream is, bit for bit, the
+ * one of the host generator: splitmix64 draws, one 32-bit half per level,
+ * a seeded bijective id scramble on [0, 2^scale), rejection of ids >= n.
+ * Errors: TC_EINVAL for scale outside [1,31], n outside [1, 2^scale],
+ * negative e0/count, NULL outputs with count > 0; TC_ECUDA.
+ */
+TC_API tc_status tc_generate_rmat(uint64_t seed, int32_t scale, int64_t n, int64_t e0,
+                           int64_t count, uint32_t t1, uint32_t t2, uint32_t t3,
+                           int32_t* src_dev, int32_t* dst_dev, void* stream);
+
+/*
+ * Kernel accounting (not part of the paper's method; measurement support).
+ *
+ * tc_kernel_launches: number of kernels this library has launched since it
+ * was loaded (all threads).
+ * tc_profile_enable: on != 0 clears the records and starts bracketing every
+ * launch with CUDA events recorded on the launching stream; 0 stops.
+ * tc_profile_read: waits for the recorded events and writes, per kernel
+ * name, the launches and summed device time since profiling was enabled.
+ * Fills at most max entries; *count receives the number of names.
+ * TC_EINVAL on NULL count (or NULL out with max > 0); TC_ECUDA.
+ */
+typedef struct {
+    char name[40];
+    int64_t launches;
+    double total_ms;
+} tc_kernel_time;
+
+TC_API long long tc_kernel_launches(void);
+TC_API void tc_profile_enable(int32_t on);
+TC_API tc_status tc_profile_read(tc_kernel_time* out, int32_t max, int32_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_H */

@@ -1,0 +1,217 @@
+// C ABI entry points: argument checks, error capture, allocation, ownership.
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+#include "tc_internal.cuh"
+
+namespace tc {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+void clear_error() { g_err[0] = 0; }
+
+void* Alloc::get(size_t bytes) {
+    void* p = nullptr;
+    if (has_user) {
+        p = user.alloc(bytes, user.ctx, stream);
+        if (!p) TC_FAIL(TC_ENOMEM, "device allocation of %zu bytes failed (caller allocator)", bytes);
+        return p;
+    }
+    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        TC_FAIL(TC_ENOMEM, "cudaMallocAsync of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    return p;
+}
+
+void Alloc::put(void* p, size_t bytes) {
+    if (!p) return;
+    if (has_user)
+        user.free(p, bytes, user.ctx, stream);
+    else
+        cudaFreeAsync(p, stream);
+}
+
+void tuning_defaults(tc_tuning* t) {
+    std::memset(t, 0, sizeof(*t));
+    t->small_max_outdeg = kSmallMaxOutdeg;
+    t->warp_unit_tasks = 256;
+    t->cta_unit_tasks = 2048;
+    t->cta_threads = 256;
+    t->slice_max = kMaxSlice;
+}
+
+void tuning_resolve(const tc_tuning* in, tc_tuning* out) {
+    tuning_defaults(out);
+    if (!in) return;
+    if (in->small_max_outdeg > 0) out->small_max_outdeg = std::min(in->small_max_outdeg, kSmallMaxOutdeg);
+    if (in->warp_unit_tasks > 0) out->warp_unit_tasks = in->warp_unit_tasks;
+    if (in->cta_unit_tasks > 0) out->cta_unit_tasks = in->cta_unit_tasks;
+    if (in->cta_threads > 0) {
+        int th = in->cta_threads;
+        th = std::max(64, std::min(1024, th));
+        out->cta_threads = (th / 32) * 32;
+    }
+    if (in->slice_max > 0) out->slice_max = std::max(64, std::min(in->slice_max, kMaxSlice));
+}
+
+bool tuning_equal(const tc_tuning& a, const tc_tuning& b) {
+    return std::memcmp(&a, &b, sizeof(tc_tuning)) == 0;
+}
+
+static void graph_release(tc_graph* g) {
+    if (!g) return;
+    try {
+        if (g->units_mem) g->alloc.put(g->units_mem, g->units_bytes);
+        if (g->arena) g->alloc.put(g->arena, g->arena_bytes);
+    } catch (const Error&) {
+    }
+    delete g;
+}
+
+}  // namespace tc
+
+using namespace tc;
+
+#define TC_API_BEGIN \
+    clear_error();   \
+    try {
+#define TC_API_END                                               \
+    }                                                            \
+    catch (const ::tc::Error& e) {                               \
+        return e.status;                                         \
+    }                                                            \
+    catch (const std::bad_alloc&) {                              \
+        set_error("host allocation failed");                     \
+        return TC_ENOMEM;                                        \
+    }                                                            \
+    catch (...) {                                                \
+        set_error("unexpected exception");                       \
+        return TC_ECUDA;                                         \
+    }                                                            \
+    return TC_OK;
+
+extern "C" {
+
+const char* tc_last_error(void) { return g_err; }
+
+tc_status tc_tuning_default(tc_tuning* out) {
+    TC_API_BEGIN
+    if (!out) TC_FAIL(TC_EINVAL, "tc_tuning_default: out is NULL");
+    tuning_defaults(out);
+    TC_API_END
+}
+
+tc_status tc_preprocess(const int32_t* src, const int32_t* dst, int64_t num_pairs, int64_t n,
+                        uint32_t flags, const tc_allocator* alloc, void* stream, tc_graph** out) {
+    TC_API_BEGIN
+    if (!out) TC_FAIL(TC_EINVAL, "tc_preprocess: out is NULL");
+    if (num_pairs < 0) TC_FAIL(TC_EINVAL, "tc_preprocess: num_pairs < 0");
+    if (n < 0 || n >= (int64_t)0x7fffffff) TC_FAIL(TC_EINVAL, "tc_preprocess: n outside [0, 2^31-1)");
+    if (num_pairs > 0 && (!src || !dst)) TC_FAIL(TC_EINVAL, "tc_preprocess: src or dst is NULL");
+    if (num_pairs > (int64_t)0x7fffffff) TC_FAIL(TC_EINVAL, "tc_preprocess: num_pairs >= 2^31");
+    if ((flags & TC_OFFSETS_32) && (flags & TC_OFFSETS_64))
+        TC_FAIL(TC_EINVAL, "tc_preprocess: both offset widths requested");
+    if (alloc && (!alloc->alloc || !alloc->free))
+        TC_FAIL(TC_EINVAL, "tc_preprocess: allocator without alloc/free");
+    tc_graph* g = new tc_graph();
+    g->n = n;
+    g->num_pairs = num_pairs;
+    g->bits = std::max(1, ceil_log2_u64((uint64_t)std::max<int64_t>(n, 1)));
+    g->alloc.stream = static_cast<cudaStream_t>(stream);
+    if (alloc) {
+        g->alloc.user = *alloc;
+        g->alloc.has_user = true;
+    }
+    g->stats.n = n;
+    g->stats.num_pairs = num_pairs;
+    try {
+        preprocess(g, src, dst, num_pairs, flags, static_cast<cudaStream_t>(stream));
+    } catch (...) {
+        graph_release(g);
+        throw;
+    }
+    *out = g;
+    TC_API_END
+}
+
+tc_status tc_count(const tc_graph* g, const tc_tuning* tune, uint64_t* total_host,
+                   uint64_t* total_dev, uint64_t* per_vertex_dev, void* stream) {
+    TC_API_BEGIN
+    if (!g) TC_FAIL(TC_EINVAL, "tc_count: graph is NULL");
+    if (!total_host && !total_dev && !per_vertex_dev)
+        TC_FAIL(TC_EINVAL, "tc_count: no output requested");
+    tc_tuning t;
+    tuning_resolve(tune, &t);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const_cast<tc_graph*>(g)->alloc.stream = st;
+    count(g, t, total_dev, per_vertex_dev, st);
+    if (total_host) {
+        unsigned long long v = 0;
+        TC_CUDA(cudaMemcpyAsync(&v, g->counters + CTR_TOTAL, sizeof(v), cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaStreamSynchronize(st));
+        *total_host = v;
+    }
+    TC_API_END
+}
+
+tc_status tc_triangles(const int32_t* src_host, const int32_t* dst_host, int64_t num_pairs,
+                       int64_t n, uint32_t flags, void* stream, uint64_t* total_host,
+                       uint64_t* per_vertex_host) {
+    TC_API_BEGIN
+    if (!total_host) TC_FAIL(TC_EINVAL, "tc_triangles: total_host is NULL");
+    if (flags & TC_INPUT_ON_DEVICE) TC_FAIL(TC_EINVAL, "tc_triangles: takes host inputs");
+    tc_graph* g = nullptr;
+    tc_status s = tc_preprocess(src_host, dst_host, num_pairs, n, flags, nullptr, stream, &g);
+    if (s != TC_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    try {
+        tc_tuning t;
+        tuning_resolve(nullptr, &t);
+        uint64_t* pv = nullptr;
+        if (per_vertex_host && n > 0) pv = static_cast<uint64_t*>(g->alloc.get(sizeof(uint64_t) * n));
+        try {
+            count(g, t, nullptr, pv, st);
+            unsigned long long v = 0;
+            TC_CUDA(cudaMemcpyAsync(&v, g->counters + CTR_TOTAL, sizeof(v), cudaMemcpyDeviceToHost, st));
+            if (pv)
+                TC_CUDA(cudaMemcpyAsync(per_vertex_host, pv, sizeof(uint64_t) * n,
+                                        cudaMemcpyDeviceToHost, st));
+            TC_CUDA(cudaStreamSynchronize(st));
+            *total_host = v;
+        } catch (...) {
+            if (pv) g->alloc.put(pv, sizeof(uint64_t) * n);
+            throw;
+        }
+        if (pv) g->alloc.put(pv, sizeof(uint64_t) * n);
+    } catch (...) {
+        graph_release(g);
+        throw;
+    }
+    graph_release(g);
+    TC_API_END
+}
+
+tc_status tc_graph_get_stats(const tc_graph* g, tc_graph_stats* out) {
+    TC_API_BEGIN
+    if (!g || !out) TC_FAIL(TC_EINVAL, "tc_graph_get_stats: NULL argument");
+    *out = g->stats;
+    out->small_units = g->n_small;
+    out->large_units = g->n_large;
+    out->device_bytes = (int64_t)(g->arena_bytes + g->units_bytes);
+    TC_API_END
+}
+
+void tc_graph_free(tc_graph* g) { graph_release(g); }
+
+}  // extern "C"

@@ -1,0 +1,189 @@
+// Internal helpers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string>
+#include <vector>
+
+#include "../../include/tc.h"
+
+namespace tc {
+
+// ---------------------------------------------------------------------------
+// error reporting: a thread-local message plus a status code
+// ---------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+void clear_error();
+
+struct Error {
+    tc_status status;
+};
+
+#define TC_FAIL(st, ...)                  \
+    do {                                  \
+        ::tc::set_error(__VA_ARGS__);     \
+        throw ::tc::Error{st};            \
+    } while (0)
+
+#define TC_CUDA(call)                                                              \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess)                                                     \
+            TC_FAIL(TC_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                    __FILE__, __LINE__);                                           \
+    } while (0)
+
+#define TC_LAUNCH_CHECK() TC_CUDA(cudaGetLastError())
+
+// Scope around one kernel launch: counts it and, when profiling is on,
+// brackets it with CUDA events on the launching stream.
+class Prof {
+public:
+    Prof(const char* name, cudaStream_t st);
+    ~Prof();
+    Prof(const Prof&) = delete;
+    Prof& operator=(const Prof&) = delete;
+
+private:
+    const char* name_;
+    cudaStream_t st_;
+    void* a_ = nullptr;
+    void* b_ = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+// device memory through the caller's allocator (or cudaMallocAsync)
+// ---------------------------------------------------------------------------
+struct Alloc {
+    tc_allocator user{};
+    bool has_user = false;
+    cudaStream_t stream = nullptr;
+
+    void* get(size_t bytes);
+    void put(void* p, size_t bytes);
+};
+
+// RAII scratch buffer on an Alloc.
+template <class T>
+struct Buf {
+    Alloc* a = nullptr;
+    T* p = nullptr;
+    size_t bytes = 0;
+    Buf() = default;
+    Buf(Alloc& al, size_t count) : a(&al), bytes(sizeof(T) * (count ? count : 1)) {
+        p = static_cast<T*>(al.get(bytes));
+    }
+    Buf(const Buf&) = delete;
+    Buf& operator=(const Buf&) = delete;
+    Buf(Buf&& o) noexcept : a(o.a), p(o.p), bytes(o.bytes) { o.p = nullptr; }
+    Buf& operator=(Buf&& o) noexcept {
+        release();
+        a = o.a; p = o.p; bytes = o.bytes; o.p = nullptr;
+        return *this;
+    }
+    ~Buf() { release(); }
+    void release() {
+        if (p && a) a->put(p, bytes);
+        p = nullptr;
+    }
+    T* get() const { return p; }
+};
+
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+
+inline int ceil_log2_u64(uint64_t x) {  // smallest b with 2^b >= x (x >= 1)
+    int b = 0;
+    while ((1ull << b) < x) ++b;
+    return b;
+}
+
+inline int num_sms() {
+    static int s = -1;
+    if (s < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+        if (s <= 0) s = 1;
+    }
+    return s;
+}
+
+inline unsigned grid_for(int64_t items, int threads, int64_t cap = 0) {
+    int64_t g = (items + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (cap > 0 && g > cap) g = cap;
+    if (g > 0x7fffffff) g = 0x7fffffff;
+    return (unsigned)g;
+}
+
+// ---------------------------------------------------------------------------
+// device-wide primitives (scan.cu, radix.cu)
+// ---------------------------------------------------------------------------
+
+// out[i] = sum_{k<i} in[i]; *total_dev (if non-null) = sum of all.  Any of
+// (int32, int64) in, int64 out.  in may alias out.
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t count, int64_t* total_dev,
+                        Alloc& al, cudaStream_t st);
+void exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t count,
+                               int64_t* total_dev, Alloc& al, cudaStream_t st);
+
+// Stable LSD radix sort of 64-bit keys on bits [lo, hi).  Sorted keys end up
+// in *keys (the two buffers may be swapped).  count <= 2^31 - 1.
+void radix_sort_u64(uint64_t** keys, uint64_t** alt, int64_t count, int lo, int hi,
+                    Alloc& al, cudaStream_t st);
+
+}  // namespace tc
+
+// The graph object behind the opaque handle.
+struct tc_graph {
+    int64_t n = 0, m = 0, num_pairs = 0;
+    int bits = 1;               // ceil(log2(n)), >= 1
+    bool off64 = false;
+    tc::Alloc alloc;
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+
+    // device views into the arena
+    void* off = nullptr;        // U offsets, n+1 (int32 or int64)
+    int32_t* adj = nullptr;     // U columns, m, rows ascending
+    int32_t* perm = nullptr;    // old id -> new label, n
+    int64_t* loff = nullptr;    // task list offsets per pivot j, n+1
+    struct Task* tasks = nullptr;   // <j,i,k> tasks grouped by pivot j
+    struct Unit* small_units = nullptr;
+    struct Unit* large_units = nullptr;
+    unsigned long long* counters = nullptr;  // queue heads and totals (device)
+    uint64_t* tnew = nullptr;   // per-vertex accumulator in new labels, n
+
+    int64_t n_tasks = 0, n_small = 0, n_large = 0;
+    int32_t large_table = 0;        // table slots a large unit needs (power of 2)
+    void* units_mem = nullptr;      // small units, then large units
+    size_t units_bytes = 0;
+    tc_tuning units_tuning{};       // tuning the unit lists were built for
+    tc_graph_stats stats{};
+};
+
+// A <j,i,k> task: edge (i,j) of U with the part of U_i after j nonempty.
+struct Task {
+    int64_t start;   // index in adj of the first entry of U_i after j
+    int32_t len;     // number of entries of U_i after j (> 0)
+    int32_t i;       // row (new label), for per-vertex credit
+};
+
+// A work unit: pivot j, a slice of U_j (for pivots larger than one table) and
+// a contiguous range of j's tasks.
+struct Unit {
+    int32_t j;
+    int32_t slice;      // slice index of U_j (entries [slice*S, slice*S+S))
+    int64_t t0;         // first task (index into tasks)
+    int64_t t1;         // one past the last task
+};
+
+enum : int {
+    CTR_SMALL_HEAD = 0,
+    CTR_LARGE_HEAD = 1,
+    CTR_TOTAL = 2,
+    CTR_COUNT = 8
+};

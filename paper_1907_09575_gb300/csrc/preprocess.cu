@@ -1,0 +1,420 @@
+// tc_preprocess: Section 5.3 of the paper on one device.
+//
+//   a1 canonicalise   pairs -> key (min << b | max); self-loops -> sentinel
+//   a2 sort + unique  LSD radix sort, keep first of each run -> E (m edges)
+//   a3 degrees        d(v) over E (warp-aggregated atomics)
+//   a4 relabel        stable sort of (d(v) << b | v) on the degree bits: the
+//                     rank is the new label (non-decreasing degree, ties by id)
+//   a5 orient + CSR   (min, max) of the new labels, sorted -> U rows ascending
+//   a6 tasks + units  <j,i,k> tasks grouped by pivot j, then work units
+//
+// b = ceil(log2 n) bits per id, so keys use 2b <= 62 bits.
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+#include "tc_internal.cuh"
+
+namespace tc {
+namespace {
+
+constexpr int kT = 256;
+
+__global__ void k_canon(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                        int64_t P, int64_t n, int bits, uint64_t sentinel,
+                        uint64_t* __restrict__ keys, int* __restrict__ err) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int32_t a = src[e], b = dst[e];
+        uint64_t k = sentinel;
+        if (a < 0 || b < 0 || (int64_t)a >= n || (int64_t)b >= n) {
+            atomicOr(err, 1);
+        } else if (a != b) {
+            uint64_t lo = (uint64_t)min(a, b), hi = (uint64_t)max(a, b);
+            k = (lo << bits) | hi;
+        }
+        keys[e] = k;
+    }
+}
+
+__global__ void k_unique_flags(const uint64_t* __restrict__ keys, int64_t P, uint64_t sentinel,
+                               int32_t* __restrict__ flags) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k = keys[e];
+        flags[e] = (k != sentinel && (e == 0 || keys[e - 1] != k)) ? 1 : 0;
+    }
+}
+
+// Adds c to counter[v] once per group of lanes holding the same v.
+__device__ __forceinline__ void warp_add(int32_t* counter, int32_t v, bool active, int c = 1) {
+    unsigned act = __ballot_sync(0xffffffffu, active);
+    if (!active) return;
+    unsigned peers = __match_any_sync(act, v);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&counter[v], c * __popc(peers));
+}
+
+__global__ void k_unique_compact(const uint64_t* __restrict__ keys, const int32_t* __restrict__ flags,
+                                 const int64_t* __restrict__ pos, int64_t P, int bits,
+                                 uint64_t* __restrict__ E, int32_t* __restrict__ deg) {
+    const uint64_t mask = (1ull << bits) - 1ull;
+    // grid-stride with whole-warp iterations so the warp intrinsics see full warps
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < P; base += stride) {
+        int64_t e = base + threadIdx.x;
+        bool keep = e < P && flags[e];
+        uint64_t k = keep ? keys[e] : 0;
+        if (keep) E[pos[e]] = k;
+        warp_add(deg, (int32_t)(k >> bits), keep);
+        warp_add(deg, (int32_t)(k & mask), keep);
+    }
+}
+
+__global__ void k_max_i32(const int32_t* __restrict__ x, int64_t n, int* __restrict__ out) {
+    int mx = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        mx = max(mx, x[v]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
+}
+
+__global__ void k_degree_keys(const int32_t* __restrict__ deg, int64_t n, int bits,
+                              uint64_t* __restrict__ keys) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        keys[v] = ((uint64_t)(uint32_t)deg[v] << bits) | (uint64_t)v;
+}
+
+__global__ void k_perm(const uint64_t* __restrict__ sorted, int64_t n, int bits,
+                       int32_t* __restrict__ perm) {
+    const uint64_t mask = (1ull << bits) - 1ull;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x)
+        perm[sorted[r] & mask] = (int32_t)r;
+}
+
+__global__ void k_orient(const uint64_t* __restrict__ E, int64_t m, int bits,
+                         const int32_t* __restrict__ perm, uint64_t* __restrict__ keys) {
+    const uint64_t mask = (1ull << bits) - 1ull;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k = E[e];
+        uint32_t u = (uint32_t)perm[k >> bits], v = (uint32_t)perm[k & mask];
+        uint64_t lo = min(u, v), hi = max(u, v);
+        keys[e] = (lo << bits) | hi;
+    }
+}
+
+// adj[e] = column; dplus[row] += 1 (rows are sorted, so lanes agree a lot)
+__global__ void k_adj_rows(const uint64_t* __restrict__ keys, int64_t m, int bits,
+                           int32_t* __restrict__ adj, int32_t* __restrict__ dplus) {
+    const uint64_t mask = (1ull << bits) - 1ull;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < m; base += stride) {
+        int64_t e = base + threadIdx.x;
+        bool ok = e < m;
+        uint64_t k = ok ? keys[e] : 0;
+        if (ok) adj[e] = (int32_t)(k & mask);
+        warp_add(dplus, (int32_t)(k >> bits), ok);
+    }
+}
+
+template <class OffT>
+__global__ void k_store_offsets(const int64_t* __restrict__ off64, int64_t count,
+                                OffT* __restrict__ out) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < count;
+         v += (int64_t)gridDim.x * blockDim.x)
+        out[v] = (OffT)off64[v];
+}
+
+// Task (i,j): edge e of U, row i, column j, with len = entries of U_i after j.
+template <class OffT>
+__global__ void k_task_count(const uint64_t* __restrict__ keys, int64_t m, int bits,
+                             const OffT* __restrict__ off, int32_t* __restrict__ tcount,
+                             unsigned long long* __restrict__ probes) {
+    const uint64_t mask = (1ull << bits) - 1ull;
+    unsigned long long my = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < m; base += stride) {
+        int64_t e = base + threadIdx.x;
+        bool has = false;
+        int32_t j = 0;
+        if (e < m) {
+            uint64_t k = keys[e];
+            int64_t i = (int64_t)(k >> bits);
+            j = (int32_t)(k & mask);
+            int64_t len = (int64_t)off[i + 1] - e - 1;
+            has = len > 0;
+            my += (unsigned long long)(len > 0 ? len : 0);
+        }
+        if (has) atomicAdd(&tcount[j], 1);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) my += __shfl_xor_sync(0xffffffffu, my, o);
+    if ((threadIdx.x & 31) == 0 && my) atomicAdd(probes, my);
+}
+
+template <class OffT>
+__global__ void k_task_fill(const uint64_t* __restrict__ keys, int64_t m, int bits,
+                            const OffT* __restrict__ off, const int64_t* __restrict__ loff,
+                            int32_t* __restrict__ cursor, Task* __restrict__ tasks) {
+    const uint64_t mask = (1ull << bits) - 1ull;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k = keys[e];
+        int64_t i = (int64_t)(k >> bits);
+        int32_t j = (int32_t)(k & mask);
+        int64_t len = (int64_t)off[i + 1] - e - 1;
+        if (len > 0) {
+            int32_t slot = atomicAdd(&cursor[j], 1);
+            Task t;
+            t.start = e + 1;
+            t.len = (int32_t)len;
+            t.i = (int32_t)i;
+            tasks[loff[j] + slot] = t;
+        }
+    }
+}
+
+template <class OffT>
+__global__ void k_max_outdeg(const OffT* __restrict__ off, int64_t n, int* __restrict__ out) {
+    int mx = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        mx = max(mx, (int)(off[v + 1] - off[v]));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+void preprocess(tc_graph* g, const int32_t* src_in, const int32_t* dst_in, int64_t P,
+                uint32_t flags, cudaStream_t st) {
+    Alloc& al = g->alloc;
+    const int64_t n = g->n;
+    const int bits = g->bits;
+    const uint64_t sentinel = (bits * 2 >= 64) ? ~0ull : ((1ull << (2 * bits)) - 1ull);
+    const unsigned G = (unsigned)(num_sms() * 8);
+
+    // input on the device
+    const int32_t* src = src_in;
+    const int32_t* dst = dst_in;
+    Buf<int32_t> hsrc, hdst;
+    if (!(flags & TC_INPUT_ON_DEVICE) && P > 0) {
+        hsrc = Buf<int32_t>(al, (size_t)P);
+        hdst = Buf<int32_t>(al, (size_t)P);
+        TC_CUDA(cudaMemcpyAsync(hsrc.get(), src_in, sizeof(int32_t) * P, cudaMemcpyHostToDevice, st));
+        TC_CUDA(cudaMemcpyAsync(hdst.get(), dst_in, sizeof(int32_t) * P, cudaMemcpyHostToDevice, st));
+        src = hsrc.get();
+        dst = hdst.get();
+    }
+
+    Buf<int> scal(al, 8);   // [0] err, [1] max degree, [2] max out-degree
+    TC_CUDA(cudaMemsetAsync(scal.get(), 0, 8 * sizeof(int), st));
+    Buf<int64_t> tot(al, 4);  // [0] m, [1] tasks
+
+    // a1 + a2: canonical keys, sorted, unique
+    Buf<uint64_t> kb(al, (size_t)std::max<int64_t>(P, 1));
+    Buf<uint64_t> ab(al, (size_t)std::max<int64_t>(P, 1));
+    uint64_t* keys = kb.get();
+    uint64_t* alt = ab.get();
+    int64_t m = 0;
+    Buf<int32_t> deg(al, (size_t)std::max<int64_t>(n, 1));
+    TC_CUDA(cudaMemsetAsync(deg.get(), 0, sizeof(int32_t) * std::max<int64_t>(n, 1), st));
+    if (P > 0) {
+        {
+            Prof prof_("k_canon", st);
+            k_canon<<<grid_for(P, kT, G), kT, 0, st>>>(src, dst, P, n, bits, sentinel, keys, scal.get());
+        }
+        TC_LAUNCH_CHECK();
+        int err = 0;
+        TC_CUDA(cudaMemcpyAsync(&err, scal.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaStreamSynchronize(st));
+        if (err) TC_FAIL(TC_EINVAL, "tc_preprocess: a vertex id lies outside [0, n)");
+        hsrc.release();
+        hdst.release();
+        radix_sort_u64(&keys, &alt, P, 0, 2 * bits, al, st);
+        {
+            Buf<int32_t> fl(al, (size_t)P);
+            Buf<int64_t> pos(al, (size_t)P);
+            {
+                Prof prof_("k_unique_flags", st);
+                k_unique_flags<<<grid_for(P, kT, G), kT, 0, st>>>(keys, P, sentinel, fl.get());
+            }
+            TC_LAUNCH_CHECK();
+            exclusive_scan_i32_to_i64(fl.get(), pos.get(), P, tot.get(), al, st);
+            {
+                Prof prof_("k_unique_compact", st);
+                k_unique_compact<<<grid_for(P, kT, G), kT, 0, st>>>(keys, fl.get(), pos.get(), P, bits,
+                                                                alt, deg.get());
+            }
+            TC_LAUNCH_CHECK();
+            TC_CUDA(cudaMemcpyAsync(&m, tot.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            TC_CUDA(cudaStreamSynchronize(st));
+        }
+        std::swap(keys, alt);  // E now in `keys`
+    }
+    g->m = m;
+    g->stats.m = m;
+    if ((flags & TC_OFFSETS_32) && m >= (int64_t)0x7fffffff)
+        TC_FAIL(TC_EINVAL, "tc_preprocess: 32-bit offsets requested but m = %lld", (long long)m);
+    g->off64 = (flags & TC_OFFSETS_64) ? true : (flags & TC_OFFSETS_32) ? false
+                                                                         : (m >= (int64_t)0x7fffffff);
+    const size_t ob = g->off64 ? 8 : 4;
+
+    // arena: off, adj, perm, loff, tasks (capacity m), counters, tnew
+    size_t sz_off = align_up(ob * (size_t)(n + 1)), sz_adj = align_up(4 * (size_t)std::max<int64_t>(m, 1));
+    size_t sz_perm = align_up(4 * (size_t)std::max<int64_t>(n, 1));
+    size_t sz_loff = align_up(8 * (size_t)(n + 1));
+    size_t sz_tasks = align_up(sizeof(Task) * (size_t)std::max<int64_t>(m, 1));
+    size_t sz_ctr = align_up(sizeof(unsigned long long) * CTR_COUNT);
+    size_t sz_tnew = align_up(8 * (size_t)std::max<int64_t>(n, 1));
+    g->arena_bytes = sz_off + sz_adj + sz_perm + sz_loff + sz_tasks + sz_ctr + sz_tnew;
+    g->arena = al.get(g->arena_bytes);
+    char* a = static_cast<char*>(g->arena);
+    g->off = a; a += sz_off;
+    g->adj = reinterpret_cast<int32_t*>(a); a += sz_adj;
+    g->perm = reinterpret_cast<int32_t*>(a); a += sz_perm;
+    g->loff = reinterpret_cast<int64_t*>(a); a += sz_loff;
+    g->tasks = reinterpret_cast<Task*>(a); a += sz_tasks;
+    g->counters = reinterpret_cast<unsigned long long*>(a); a += sz_ctr;
+    g->tnew = reinterpret_cast<uint64_t*>(a);
+
+    // a3 max degree, a4 relabel
+    int maxdeg = 0;
+    if (n > 0) {
+        {
+            Prof prof_("k_max_i32", st);
+            k_max_i32<<<grid_for(n, kT, G), kT, 0, st>>>(deg.get(), n, scal.get() + 1);
+        }
+        TC_LAUNCH_CHECK();
+        TC_CUDA(cudaMemcpyAsync(&maxdeg, scal.get() + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaStreamSynchronize(st));
+        Buf<uint64_t> dk(al, (size_t)n), da(al, (size_t)n);
+        uint64_t* dkeys = dk.get();
+        uint64_t* dalt = da.get();
+        {
+            Prof prof_("k_degree_keys", st);
+            k_degree_keys<<<grid_for(n, kT, G), kT, 0, st>>>(deg.get(), n, bits, dkeys);
+        }
+        TC_LAUNCH_CHECK();
+        int dbits = ceil_log2_u64((uint64_t)maxdeg + 1);
+        radix_sort_u64(&dkeys, &dalt, n, bits, bits + dbits, al, st);
+        {
+            Prof prof_("k_perm", st);
+            k_perm<<<grid_for(n, kT, G), kT, 0, st>>>(dkeys, n, bits, g->perm);
+        }
+        TC_LAUNCH_CHECK();
+    }
+    g->stats.max_deg = maxdeg;
+    deg.release();
+
+    // a5 orient and build U
+    Buf<int32_t> dplus(al, (size_t)std::max<int64_t>(n, 1));
+    TC_CUDA(cudaMemsetAsync(dplus.get(), 0, sizeof(int32_t) * std::max<int64_t>(n, 1), st));
+    Buf<int64_t> off64(al, (size_t)(n + 1));
+    if (m > 0) {
+        {
+            Prof prof_("k_orient", st);
+            k_orient<<<grid_for(m, kT, G), kT, 0, st>>>(keys, m, bits, g->perm, alt);
+        }
+        TC_LAUNCH_CHECK();
+        std::swap(keys, alt);
+        radix_sort_u64(&keys, &alt, m, 0, 2 * bits, al, st);
+        {
+            Prof prof_("k_adj_rows", st);
+            k_adj_rows<<<grid_for(m, kT, G), kT, 0, st>>>(keys, m, bits, g->adj, dplus.get());
+        }
+        TC_LAUNCH_CHECK();
+    }
+    // off = exclusive scan of dplus, with off[n] = m
+    exclusive_scan_i32_to_i64(dplus.get(), off64.get(), n, off64.get() + n, al, st);
+    if (g->off64) {
+        TC_CUDA(cudaMemcpyAsync(g->off, off64.get(), 8 * (size_t)(n + 1), cudaMemcpyDeviceToDevice, st));
+    } else {
+        {
+            Prof prof_("k_store_offsets", st);
+            k_store_offsets<int32_t><<<grid_for(n + 1, kT, G), kT, 0, st>>>(
+            off64.get(), n + 1, static_cast<int32_t*>(g->off));
+        }
+        TC_LAUNCH_CHECK();
+    }
+
+    // a6 tasks grouped by pivot j
+    Buf<unsigned long long> probes(al, 1);
+    TC_CUDA(cudaMemsetAsync(probes.get(), 0, sizeof(unsigned long long), st));
+    int32_t* tcount = dplus.get();  // reuse
+    TC_CUDA(cudaMemsetAsync(tcount, 0, sizeof(int32_t) * std::max<int64_t>(n, 1), st));
+    if (m > 0) {
+        if (g->off64)
+            {
+                Prof prof_("k_task_count", st);
+                k_task_count<int64_t><<<grid_for(m, kT, G), kT, 0, st>>>(
+                keys, m, bits, static_cast<const int64_t*>(g->off), tcount, probes.get());
+            }
+        else
+            {
+                Prof prof_("k_task_count", st);
+                k_task_count<int32_t><<<grid_for(m, kT, G), kT, 0, st>>>(
+                keys, m, bits, static_cast<const int32_t*>(g->off), tcount, probes.get());
+            }
+        TC_LAUNCH_CHECK();
+    }
+    exclusive_scan_i32_to_i64(tcount, g->loff, n, g->loff + n, al, st);
+    TC_CUDA(cudaMemsetAsync(tcount, 0, sizeof(int32_t) * std::max<int64_t>(n, 1), st));
+    if (m > 0) {
+        if (g->off64)
+            {
+                Prof prof_("k_task_fill", st);
+                k_task_fill<int64_t><<<grid_for(m, kT, G), kT, 0, st>>>(
+                keys, m, bits, static_cast<const int64_t*>(g->off), g->loff, tcount, g->tasks);
+            }
+        else
+            {
+                Prof prof_("k_task_fill", st);
+                k_task_fill<int32_t><<<grid_for(m, kT, G), kT, 0, st>>>(
+                keys, m, bits, static_cast<const int32_t*>(g->off), g->loff, tcount, g->tasks);
+            }
+        TC_LAUNCH_CHECK();
+    }
+    int maxout = 0;
+    if (n > 0) {
+        if (g->off64)
+            {
+                Prof prof_("k_max_outdeg", st);
+                k_max_outdeg<int64_t><<<grid_for(n, kT, G), kT, 0, st>>>(
+                static_cast<const int64_t*>(g->off), n, scal.get() + 2);
+            }
+        else
+            {
+                Prof prof_("k_max_outdeg", st);
+                k_max_outdeg<int32_t><<<grid_for(n, kT, G), kT, 0, st>>>(
+                static_cast<const int32_t*>(g->off), n, scal.get() + 2);
+            }
+        TC_LAUNCH_CHECK();
+    }
+    unsigned long long hprobes = 0;
+    int64_t ntasks = 0;
+    TC_CUDA(cudaMemcpyAsync(&maxout, scal.get() + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaMemcpyAsync(&hprobes, probes.get(), sizeof(hprobes), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaMemcpyAsync(&ntasks, g->loff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    g->n_tasks = ntasks;
+    g->stats.max_outdeg = maxout;
+    g->stats.tasks = ntasks;
+    g->stats.probes = hprobes;
+    g->stats.offset_bytes = (int32_t)ob;
+
+    // work units for the default tuning
+    tc_tuning def;
+    tuning_defaults(&def);
+    build_units(g, def, st);
+    g->stats.device_bytes = (int64_t)(g->arena_bytes + g->units_bytes);
+}
+
+}  // namespace tc

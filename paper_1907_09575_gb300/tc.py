@@ -1,0 +1,267 @@
+"""Python binding of the C ABI in ``include/tc.h`` (argument marshalling only).
+
+Every step of preprocessing and counting runs in the CUDA library
+``_build/libtc.so``; this module only converts tensors to pointers, passes
+the current torch CUDA stream, and turns status codes into exceptions.  There
+is no CPU fallback: if the library is missing, loading fails loudly.
+
+Names follow the C functions: ``preprocess`` -> ``tc_preprocess``,
+``Graph.count`` -> ``tc_count``, ``triangles`` -> ``tc_triangles``,
+``generate_rmat`` -> ``tc_generate_rmat``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libtc.so")
+
+TC_OK, TC_EINVAL, TC_ENOMEM, TC_ECUDA, TC_ETIMEOUT, TC_EBUSY, TC_EUNSUPPORTED = range(7)
+TC_INPUT_ON_DEVICE = 0x1
+TC_OFFSETS_32 = 0x2
+TC_OFFSETS_64 = 0x4
+
+_STATUS = {1: "TC_EINVAL", 2: "TC_ENOMEM", 3: "TC_ECUDA", 4: "TC_ETIMEOUT", 5: "TC_EBUSY",
+           6: "TC_EUNSUPPORTED"}
+
+
+class TCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("small_max_outdeg", ctypes.c_int32), ("warp_unit_tasks", ctypes.c_int32),
+                ("cta_unit_tasks", ctypes.c_int32), ("cta_threads", ctypes.c_int32),
+                ("slice_max", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class GraphStats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("num_pairs", ctypes.c_int64), ("m", ctypes.c_int64),
+                ("max_deg", ctypes.c_int64), ("max_outdeg", ctypes.c_int64),
+                ("tasks", ctypes.c_int64), ("probes", ctypes.c_uint64),
+                ("small_units", ctypes.c_int64), ("large_units", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("offset_bytes", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
+class Allocator(ctypes.Structure):
+    _fields_ = [("alloc", ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                           ctypes.c_void_p)),
+                ("free", ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                          ctypes.c_void_p)),
+                ("ctx", ctypes.c_void_p)]
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+# Every symbol include/tc.h declares (checked by the tests).
+EXPORTS = ("tc_preprocess", "tc_count", "tc_triangles", "tc_graph_get_stats", "tc_graph_free",
+           "tc_tuning_default", "tc_last_error", "tc_generate_rmat", "tc_kernel_launches",
+           "tc_profile_enable", "tc_profile_read")
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double)]
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library (no fallback: raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as "
+                           "g; g.build()'` (the CUDA library is required; there is no CPU path)")
+    lib = ctypes.CDLL(path)
+    vp, i64, u32, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint64
+    st = ctypes.c_int
+    lib.tc_preprocess.argtypes = [vp, vp, i64, i64, u32, vp, vp, ctypes.POINTER(vp)]
+    lib.tc_preprocess.restype = st
+    lib.tc_count.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.tc_count.restype = st
+    lib.tc_triangles.argtypes = [vp, vp, i64, i64, u32, vp, vp, vp]
+    lib.tc_triangles.restype = st
+    lib.tc_graph_get_stats.argtypes = [vp, ctypes.POINTER(GraphStats)]
+    lib.tc_graph_get_stats.restype = st
+    lib.tc_graph_free.argtypes = [vp]
+    lib.tc_graph_free.restype = None
+    lib.tc_tuning_default.argtypes = [ctypes.POINTER(Tuning)]
+    lib.tc_tuning_default.restype = st
+    lib.tc_last_error.argtypes = []
+    lib.tc_last_error.restype = ctypes.c_char_p
+    lib.tc_generate_rmat.argtypes = [u64, i32, i64, i64, i64, u32, u32, u32, vp, vp, vp]
+    lib.tc_generate_rmat.restype = st
+    lib.tc_kernel_launches.argtypes = []
+    lib.tc_kernel_launches.restype = ctypes.c_longlong
+    lib.tc_profile_enable.argtypes = [i32]
+    lib.tc_profile_enable.restype = None
+    lib.tc_profile_read.argtypes = [ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)]
+    lib.tc_profile_read.restype = st
+    _lib = lib
+    return lib
+
+
+def _check(status: int) -> None:
+    if status != TC_OK:
+        msg = load().tc_last_error()
+        raise TCError(status, msg.decode() if msg else "")
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(x) -> tuple[int, bool]:
+    """(address, on_device) of a contiguous int32 torch tensor or numpy array."""
+    if isinstance(x, np.ndarray):
+        assert x.dtype == np.int32 and x.flags["C_CONTIGUOUS"], "need contiguous int32"
+        return x.ctypes.data, False
+    import torch
+    if isinstance(x, torch.Tensor):
+        assert x.dtype == torch.int32 and x.is_contiguous(), "need contiguous int32"
+        return x.data_ptr(), x.is_cuda
+    raise TypeError(type(x))
+
+
+def kernel_launches() -> int:
+    """Kernels this library has launched since it was loaded."""
+    return int(load().tc_kernel_launches())
+
+
+def profile_enable(on: bool = True) -> None:
+    """Start (clearing old records) or stop CUDA-event timing of every launch."""
+    load().tc_profile_enable(1 if on else 0)
+
+
+def profile_read() -> dict:
+    """{kernel name: (launches, total device ms)} since profiling was enabled."""
+    cnt = ctypes.c_int32(0)
+    _check(load().tc_profile_read(None, 0, ctypes.byref(cnt)))
+    buf = (KernelTime * max(cnt.value, 1))()
+    _check(load().tc_profile_read(buf, cnt.value, ctypes.byref(cnt)))
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
+            for i in range(cnt.value)}
+
+
+def tuning_default() -> Tuning:
+    t = Tuning()
+    _check(load().tc_tuning_default(ctypes.byref(t)))
+    return t
+
+
+class Graph:
+    """A preprocessed graph (owns the library's device arena)."""
+
+    def __init__(self, handle: int, n: int):
+        self._h = ctypes.c_void_p(handle)
+        self.n = n
+
+    @property
+    def handle(self) -> int:
+        return self._h.value or 0
+
+    def free(self) -> None:
+        if self._h.value:
+            load().tc_graph_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        s = GraphStats()
+        _check(load().tc_graph_get_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in GraphStats._fields_ if f != "pad"}
+
+    def count(self, per_vertex=None, total_dev=None, tuning: Optional[Tuning] = None,
+              stream=None, sync: bool = True):
+        """tc_count.  ``per_vertex``: None, True (allocate) or a CUDA uint64
+        tensor of n entries (int64 accepted).  ``total_dev``: optional CUDA
+        uint64/int64 tensor of one entry.  Returns the total (int) when sync,
+        else None; with per_vertex=True also returns the tensor."""
+        import torch
+        pv = per_vertex
+        if pv is True:
+            pv = torch.empty(max(self.n, 1), dtype=torch.int64, device="cuda")
+        total = ctypes.c_uint64(0)
+        st = _stream_ptr(stream)
+        _check(load().tc_count(self._h, ctypes.byref(tuning) if tuning is not None else None,
+                               ctypes.addressof(total) if sync else None,
+                               total_dev.data_ptr() if total_dev is not None else None,
+                               pv.data_ptr() if pv is not None else None, st))
+        t = int(total.value) if sync else None
+        if per_vertex is True:
+            return t, pv[: self.n]
+        return t
+
+
+def preprocess(src, dst, n: int, offsets: Optional[int] = None, stream=None,
+               allocator: Optional[Allocator] = None) -> Graph:
+    """tc_preprocess.  src/dst: int32 CUDA tensors (device input) or int32
+    numpy arrays / CPU tensors (host input, copied by the library)."""
+    ps, dev_s = _ptr(src)
+    pd, dev_d = _ptr(dst)
+    assert dev_s == dev_d, "src and dst must live on the same side"
+    num = int(src.shape[0])
+    assert int(dst.shape[0]) == num
+    flags = TC_INPUT_ON_DEVICE if dev_s else 0
+    if offsets == 32:
+        flags |= TC_OFFSETS_32
+    elif offsets == 64:
+        flags |= TC_OFFSETS_64
+    h = ctypes.c_void_p(0)
+    _check(load().tc_preprocess(ps, pd, num, n, flags,
+                                ctypes.byref(allocator) if allocator is not None else None,
+                                _stream_ptr(stream), ctypes.byref(h)))
+    return Graph(h.value, n)
+
+
+def triangles(src: np.ndarray, dst: np.ndarray, n: int, per_vertex: bool = False,
+              offsets: Optional[int] = None, stream=None):
+    """tc_triangles on host arrays; returns total (and per-vertex numpy)."""
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    total = ctypes.c_uint64(0)
+    pv = np.zeros(max(n, 1), dtype=np.uint64) if per_vertex else None
+    flags = {None: 0, 32: TC_OFFSETS_32, 64: TC_OFFSETS_64}[offsets]
+    _check(load().tc_triangles(src.ctypes.data, dst.ctypes.data, src.shape[0], n, flags,
+                               _stream_ptr(stream), ctypes.addressof(total),
+                               pv.ctypes.data if pv is not None else None))
+    if per_vertex:
+        return int(total.value), pv[:n]
+    return int(total.value)
+
+
+def generate_rmat(seed: int, scale: int, num_pairs: int, n: Optional[int] = None, e0: int = 0,
+                  thresholds: Optional[tuple[int, int, int]] = None, out=None, stream=None):
+    """tc_generate_rmat into (src, dst) int32 CUDA tensors (allocated if out is None)."""
+    import torch
+    if n is None:
+        n = 1 << scale
+    if thresholds is None:
+        from .inputs import rmat_thresholds
+        thresholds = rmat_thresholds()
+    if out is None:
+        src = torch.empty(num_pairs, dtype=torch.int32, device="cuda")
+        dst = torch.empty(num_pairs, dtype=torch.int32, device="cuda")
+    else:
+        src, dst = out
+    t1, t2, t3 = thresholds
+    _check(load().tc_generate_rmat(seed & (2**64 - 1), scale, n, e0, num_pairs, t1, t2, t3,
+                                   src.data_ptr(), dst.data_ptr(), _stream_ptr(stream)))
+    return src, dst
