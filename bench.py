@@ -1,0 +1,451 @@
+#!/usr/bin/env python
+"""Benchmark: exact triangle counting on one GB300 per rank.
+
+One step is the whole hot path on one synthetic graph already resident in
+HBM: tc_preprocess (simple-graph conversion, degree-order relabel, U CSR,
+task lists, units) followed by tc_count (total, and per-vertex counts where
+the workload asks for them).  The metric is undirected edges per second:
+m (simple undirected edges, nnz(U)) / step time, summed over ranks.
+
+Workloads (seeded, synthetic, shaped like the paper's graph500 RMAT graphs,
+with a Chung-Lu power-law graph standing in for its skewed social graphs):
+  rmat-s26   RMAT scale 26, edge factor 16, a/b/c/d .57/.19/.19/.05,
+             int64 offsets, total + per-vertex counts          (default)
+  rmat-s14   RMAT scale 14, edge factor 16, int32 offsets, total only
+  chunglu    Chung-Lu, n = 50M, exponent 2.1, mean degree 40,
+             expected degrees capped at 1M, int64 offsets, total only
+
+Multi-GPU: replicas only (each rank counts its own graph, seed + rank; no
+collective on the data path).  Printed: one JSON line from rank 0.
+
+--impl reference times the CPU oracle (single thread) on a bounded sample of
+the same workload: a smaller RMAT graph of the same family.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "rmat-s26": dict(kind="rmat", scale=26, edge_factor=16, offsets=64, per_vertex=True,
+                     desc="RMAT scale 26 (67,108,864 vertices), edge factor 16 "
+                          "(1,073,741,824 generated pairs), a/b/c/d=0.57/0.19/0.19/0.05; "
+                          "int64 offsets; total + per-vertex uint64 counts"),
+    "rmat-s14": dict(kind="rmat", scale=14, edge_factor=16, offsets=32, per_vertex=False,
+                     desc="RMAT scale 14 (16,384 vertices), edge factor 16 (262,144 generated "
+                          "pairs), a/b/c/d=0.57/0.19/0.19/0.05; int32 offsets; total count"),
+    "chunglu": dict(kind="chung_lu", n=50_000_000, gamma=2.1, mean_degree=40.0, wmax=1e6,
+                    offsets=64, per_vertex=False,
+                    desc="Chung-Lu power law, 50,000,000 vertices, exponent 2.1, mean expected "
+                         "degree 40 (10^9 pairs), expected degree capped at 10^6; int64 offsets; "
+                         "total count"),
+}
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat-s26")
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-scale", type=int, default=19,
+                    help="RMAT scale of the oracle's bounded sample")
+    ap.add_argument("--scale", type=int, default=None,
+                    help="override the RMAT scale of the workload (small profiling cases)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# helpers
+# ----------------------------------------------------------------------------
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def peaks() -> tuple[float, str]:
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback 6.8 TB/s"
+
+
+def source_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1907_09575_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            h.update(name.encode())
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel: str, workload: str, units: float):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
+    by units processed when the capture was a smaller case; None when absent
+    or when the kernel sources changed since the capture."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None, "no ncu capture committed"
+    e = rec.get(kernel)
+    if not e or e.get("source_digest") != source_digest():
+        return None, "kernel changed since the ncu capture" if e else "no capture of this kernel"
+    per_unit = e["dram_bytes"] / max(e["units"], 1)
+    return per_unit * units, f"ncu capture of {e['case']} scaled by units ({e['unit_name']})"
+
+
+def alg_bytes_count(kstats: dict, idx: int, off_bytes: int, per_vertex: bool) -> float:
+    """Algorithmic bytes of one count kernel launch (index 0 warp kernel, 1 CTA
+    kernel): per unit its record (24 B) and the pivot row bounds (2 offsets);
+    per staged pivot entry 4 B; per task its record (16 B); per probe the 4-B
+    entry of U_i read.  Per-vertex flushes are not counted (atomics)."""
+    return (kstats["units"][idx] * (24 + 2 * off_bytes) + 4 * kstats["staged"][idx]
+            + 16 * kstats["tasks"][idx] + 4 * kstats["probes"][idx])
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the CPU oracle on a bounded sample
+# ----------------------------------------------------------------------------
+
+def run_reference(args, wl):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1907_09575_gb300 import inputs
+    oracle.build()
+    scale = args.cpu_sample_scale - 1   # per step: a sample the oracle counts in a few seconds
+    spec = inputs.rmat_graph(args.seed, scale, 16)
+    src, dst = spec.generate()
+    times, m = [], 0
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        total, st = oracle.count(src, dst, spec.n, stats=True)
+        dt = time.perf_counter() - t0
+        m = st["m"]
+        if it >= args.warmup:
+            times.append(dt)
+    step_s = sum(times) / len(times)
+    value = m / step_s
+    sample = (f"RMAT scale {scale}, edge factor 16 ({spec.num_pairs} pairs, m={m}) per step: "
+              f"the oracle's full preprocess+count, single thread")
+    line = {
+        "impl": "reference", "metric": "undirected edges/sec (exact triangle count)",
+        "value": value, "unit": "edges/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def make_inputs(wl, seed, torch, tc, inputs):
+    if wl["kind"] == "rmat":
+        n = 1 << wl["scale"]
+        num = wl["edge_factor"] * n
+        s, d = tc.generate_rmat(seed, wl["scale"], num)
+        return s, d, n, num, "device-generated seeded RMAT"
+    spec = inputs.chung_lu_graph(seed, wl["n"], wl["gamma"], wl["mean_degree"], wl["wmax"])
+    hs, hd = spec.generate()
+    return (torch.from_numpy(hs).cuda(), torch.from_numpy(hd).cuda(), spec.n, spec.num_pairs,
+            "host-generated seeded Chung-Lu, uploaded before timing")
+
+
+def cpu_baseline(args):
+    import oracle
+    from paper_1907_09575_gb300 import inputs
+    oracle.build()
+    spec = inputs.rmat_graph(args.seed, args.cpu_sample_scale, 16)
+    src, dst = spec.generate()
+    t0 = time.perf_counter()
+    total, st = oracle.count(src, dst, spec.n, stats=True)
+    dt = time.perf_counter() - t0
+    return {"value": st["m"] / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": f"RMAT scale {args.cpu_sample_scale}, edge factor 16 ({spec.num_pairs} pairs, "
+                      f"m={st['m']}, {total} triangles): the oracle's preprocess+count, "
+                      f"single thread, {dt:.1f} s", "seconds": dt}
+
+
+def run_ours(args, wl):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1907_09575_gb300 import inputs, tc
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    tc.load()
+    seed = args.seed + rank
+    src, dst, n, num_pairs, data = make_inputs(wl, seed, torch, tc, inputs)
+    pv = torch.empty(max(n, 1), dtype=torch.int64, device="cuda") if wl["per_vertex"] else None
+    tdev = torch.zeros(1, dtype=torch.int64, device="cuda")
+    off = wl["offsets"]
+
+    def step():
+        g = tc.preprocess(src, dst, n, offsets=off)
+        g.count(per_vertex=pv, total_dev=tdev, sync=False)
+        return g
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    facts = None
+    for _ in range(args.warmup):
+        g = step()
+        facts = g.stats()
+        g.free()
+    torch.cuda.synchronize()
+    g = step()
+    facts = g.stats()
+    total = int(tdev.item())
+    g.free()
+
+    # --- timed region: K whole steps -------------------------------------
+    sampler = ClockSampler(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    tc.profile_enable(True)
+    l0 = tc.kernel_launches()
+    ev0.record()
+    for _ in range(args.steps):
+        g = step()
+        g.free()
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier()
+    launches = tc.kernel_launches() - l0
+    prof = tc.profile_read()
+    tc.profile_enable(False)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([ms, float(facts["m"])], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        ms, m_all = float(tmax[0]), float(tsum[1])
+    else:
+        m_all = float(facts["m"])
+    value = m_all / (ms / 1e3)
+
+    # --- count alone (the paper's "tct"), CSR resident -------------------
+    g = tc.preprocess(src, dst, n, offsets=off)
+    for _ in range(2):
+        g.count(per_vertex=pv, total_dev=tdev, sync=False)
+    torch.cuda.synchronize()
+    tc.profile_enable(True)
+    ev0.record()
+    for _ in range(args.steps):
+        g.count(per_vertex=pv, total_dev=tdev, sync=False)
+    ev1.record()
+    torch.cuda.synchronize()
+    cprof = tc.profile_read()
+    tc.profile_enable(False)
+    count_ms = ev0.elapsed_time(ev1) / args.steps
+    kst = g.count_stats()
+    g.free()
+
+    # --- roofline of the dominant kernel of the step ---------------------
+    hbm, peak_src = peaks()
+    step_kernel_ms = sum(v[1] for v in prof.values())
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    kname, (klaunch, kms) = top
+    roof = None
+    if kname in ("k_count_large", "k_count_small"):
+        idx = 1 if kname == "k_count_large" else 0
+        b_launch = alg_bytes_count(kst, idx, facts["offset_bytes"], wl["per_vertex"])
+        avg_ms = kms / klaunch
+        achieved = b_launch / (avg_ms / 1e3) / 1e9
+        traffic, tnote = traffic_for(kname, args.workload, kst["probes"][idx])
+        roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                "traffic_note": tnote, "peak_source": peak_src,
+                "alg_bytes_per_launch": b_launch, "avg_launch_ms": avg_ms,
+                "share_of_step_kernel_time": kms / step_kernel_ms,
+                "probes_per_launch": kst["probes"][idx]}
+    else:
+        roof = {"kernel": kname, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
+                "frac": None, "traffic": None, "peak_source": peak_src,
+                "share_of_step_kernel_time": kms / step_kernel_ms,
+                "note": "dominant kernel is a preprocessing kernel"}
+
+    # --- end to end through the one-shot C ABI call, host buffers ------------
+    e2e = None
+    if not args.no_e2e:
+        hs = torch.empty(num_pairs, dtype=torch.int32, pin_memory=True)
+        hd = torch.empty(num_pairs, dtype=torch.int32, pin_memory=True)
+        hs.copy_(src)
+        hd.copy_(dst)
+        hpv = torch.empty(max(n, 1), dtype=torch.int64, pin_memory=True) if wl["per_vertex"] else None
+        hs_np, hd_np = hs.numpy(), hd.numpy()
+        hpv_np = hpv.numpy() if hpv is not None else None
+        tc.triangles(hs_np, hd_np, n, per_vertex=wl["per_vertex"], offsets=off, out=hpv_np)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            r = tc.triangles(hs_np, hd_np, n, per_vertex=wl["per_vertex"], offsets=off, out=hpv_np)
+        torch.cuda.synchronize()
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        if ws > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt[0])
+        e2e_total = r[0] if isinstance(r, tuple) else r
+        assert e2e_total == total, (e2e_total, total)
+        e2e = {"value": m_all / e2e_s, "unit": "edges/s", "ms_per_step": e2e_s * 1e3,
+               "h2d_bytes_per_step": 8 * num_pairs,
+               "d2h_bytes_per_step": 8 + (8 * n if wl["per_vertex"] else 0),
+               "call": "tc_triangles (host pairs in pinned memory -> host total"
+                       + (" + per-vertex)" if wl["per_vertex"] else ")")}
+        del hs, hd, hpv
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args)
+
+    if ws > 1:
+        dist.barrier()
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    top_kernels = sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]
+    line = {
+        "metric": "undirected edges/sec (exact triangle count: preprocess + count per step)",
+        "value": value, "unit": "edges/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32 ids / uint64 counts",
+        "data": f"synthetic ({data})",
+        "config": {"workload": args.workload, "desc": wl["desc"], "n": n, "num_pairs": num_pairs,
+                   "m": facts["m"], "offsets": facts["offset_bytes"] * 8,
+                   "per_vertex": wl["per_vertex"], "seed": args.seed,
+                   "l2": f"inputs larger than L2 ({8 * num_pairs / 1e9:.2f} GB of pairs per step)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "triangles": total,
+        "count_only": {"value": m_all / (count_ms / 1e3), "unit": "edges/s", "ms": count_ms,
+                       "kernels": {k: [v[0], round(v[1], 3)] for k, v in cprof.items()}},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "graph": {k: facts[k] for k in ("m", "max_deg", "max_outdeg", "tasks", "probes",
+                                        "small_units", "large_units", "device_bytes")},
+        "count_work": kst,
+        "step_kernels_ms": {k: [v[0], round(v[1], 3)] for k, v in top_kernels},
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    wl = dict(WORKLOADS[args.workload])
+    if args.scale is not None:
+        assert wl["kind"] == "rmat", "--scale applies to the RMAT workloads"
+        wl["scale"] = args.scale
+        wl["desc"] = f"{wl['desc']} [scale overridden to {args.scale}]"
+        args.workload = f"{args.workload}@scale{args.scale}"
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

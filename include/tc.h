@@ -75,10 +75,10 @@ typedef struct {
  * depends on them; only speed does. */
 typedef struct {
     int32_t small_max_outdeg;  /* pivots with |U_j| <= this go to warp units (<= 64) */
-    int32_t warp_unit_tasks;   /* tasks per warp unit */
-    int32_t cta_unit_tasks;    /* tasks per CTA unit */
-    int32_t cta_threads;       /* threads per CTA of the large-pivot kernel (128..1024) */
-    int32_t slice_max;         /* pivot entries hashed at once by one CTA (<= 8192) */
+    int32_t warp_unit_tasks;   /* tasks per warp unit (<= 65535) */
+    int32_t cta_unit_tasks;    /* tasks per CTA unit (<= 65535) */
+    int32_t cta_threads;       /* threads per CTA of the large-pivot kernel (64..1024) */
+    int32_t slice_max;         /* pivot entries tabled at once by one CTA (64..4096) */
     int32_t reserved[3];
 } tc_tuning;
 
@@ -155,6 +155,21 @@ TC_API tc_status tc_count(const tc_graph* g, const tc_tuning* tune, uint64_t* to
 TC_API tc_status tc_triangles(const int32_t* src_host, const int32_t* dst_host, int64_t num_pairs,
                        int64_t n, uint32_t flags, void* stream, uint64_t* total_host,
                        uint64_t* per_vertex_host);
+
+/* Work done by the last tc_count on a graph, read from device counters:
+ * index 0 is the warp kernel (pivots with |U_j| <= small_max_outdeg), index 1
+ * the CTA kernel.  probes = entries of the rows U_i read and looked up. */
+typedef struct {
+    uint64_t triangles;
+    uint64_t units[2];    /* work units processed */
+    uint64_t tasks[2];    /* <j,i,k> tasks processed */
+    uint64_t probes[2];   /* table lookups (tail entries read) */
+    uint64_t staged[2];   /* pivot entries inserted into tables */
+} tc_count_stats;
+
+/* Reads the counters of the graph's last tc_count (synchronises the
+ * stream).  TC_EINVAL on NULL arguments; TC_ECUDA. */
+TC_API tc_status tc_count_get_stats(const tc_graph* g, tc_count_stats* out, void* stream);
 
 /* Fills *out with the graph's facts.  TC_EINVAL on NULL arguments. */
 TC_API tc_status tc_graph_get_stats(const tc_graph* g, tc_graph_stats* out);

@@ -55,8 +55,8 @@ void tuning_resolve(const tc_tuning* in, tc_tuning* out) {
     tuning_defaults(out);
     if (!in) return;
     if (in->small_max_outdeg > 0) out->small_max_outdeg = std::min(in->small_max_outdeg, kSmallMaxOutdeg);
-    if (in->warp_unit_tasks > 0) out->warp_unit_tasks = in->warp_unit_tasks;
-    if (in->cta_unit_tasks > 0) out->cta_unit_tasks = in->cta_unit_tasks;
+    if (in->warp_unit_tasks > 0) out->warp_unit_tasks = std::min(in->warp_unit_tasks, kMaxUnitTasks);
+    if (in->cta_unit_tasks > 0) out->cta_unit_tasks = std::min(in->cta_unit_tasks, kMaxUnitTasks);
     if (in->cta_threads > 0) {
         int th = in->cta_threads;
         th = std::max(64, std::min(1024, th));
@@ -209,6 +209,23 @@ tc_status tc_graph_get_stats(const tc_graph* g, tc_graph_stats* out) {
     out->small_units = g->n_small;
     out->large_units = g->n_large;
     out->device_bytes = (int64_t)(g->arena_bytes + g->units_bytes);
+    TC_API_END
+}
+
+tc_status tc_count_get_stats(const tc_graph* g, tc_count_stats* out, void* stream) {
+    TC_API_BEGIN
+    if (!g || !out) TC_FAIL(TC_EINVAL, "tc_count_get_stats: NULL argument");
+    unsigned long long c[CTR_COUNT];
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    TC_CUDA(cudaMemcpyAsync(c, g->counters, sizeof(c), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    out->triangles = c[CTR_TOTAL];
+    for (int k = 0; k < 2; ++k) {
+        out->units[k] = c[CTR_UNITS + k];
+        out->tasks[k] = c[CTR_TASKS + k];
+        out->probes[k] = c[CTR_PROBES + k];
+        out->staged[k] = c[CTR_STAGED + k];
+    }
     TC_API_END
 }
 

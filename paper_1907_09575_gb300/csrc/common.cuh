@@ -158,7 +158,6 @@ struct tc_graph {
     uint64_t* tnew = nullptr;   // per-vertex accumulator in new labels, n
 
     int64_t n_tasks = 0, n_small = 0, n_large = 0;
-    int32_t large_table = 0;        // table slots a large unit needs (power of 2)
     void* units_mem = nullptr;      // small units, then large units
     size_t units_bytes = 0;
     tc_tuning units_tuning{};       // tuning the unit lists were built for
@@ -181,9 +180,15 @@ struct Unit {
     int64_t t1;         // one past the last task
 };
 
+// Device counters of one count: queue heads, the total, and work done by the
+// warp kernel (index 0) and the CTA kernel (index 1).
 enum : int {
     CTR_SMALL_HEAD = 0,
     CTR_LARGE_HEAD = 1,
     CTR_TOTAL = 2,
-    CTR_COUNT = 8
+    CTR_UNITS = 3,    // +0 warp, +1 CTA
+    CTR_TASKS = 5,
+    CTR_PROBES = 7,
+    CTR_STAGED = 9,
+    CTR_COUNT = 16
 };

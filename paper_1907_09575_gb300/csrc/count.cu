@@ -34,8 +34,18 @@ namespace {
 
 constexpr int kSmallWarps = 8;
 constexpr int kSmallThreads = kSmallWarps * 32;
-constexpr int kGrab = 4;   // warp units popped per queue access
+constexpr int kGrab = 4;          // warp units popped per queue access
 constexpr int kEmpty = -1;
+constexpr int kUnroll = 4;        // independent loads in flight per lane
+// warp unit table region: 128 hash slots, or a 128-word bitmap (4096 labels)
+// plus its 128 16-bit rank prefixes
+constexpr int kSmallBitWords = 128;
+constexpr int kSmallRegionWords = kSmallBitWords + kSmallBitWords / 2;
+// CTA unit table region (32-bit words): hash slots <= 2 * slice <= 8192, or a
+// bitmap of kBitWords words (kBitWords * 32 labels) plus 16-bit prefixes
+constexpr int kBitWords = 5120;
+constexpr int kRegionWords = 8192;
+static_assert(kBitWords + kBitWords / 2 <= kRegionWords, "bitmap + prefix fit the region");
 
 __device__ __forceinline__ int64_t shfl64(int64_t v, int src) {
     return __shfl_sync(0xffffffffu, v, src);
@@ -51,116 +61,210 @@ __device__ __forceinline__ int warp_incl_scan_i32(int v) {
     return v;
 }
 
-__device__ __forceinline__ void table_insert(int* tab, unsigned mask, bool direct, int lo, int k) {
-    if (direct) {
-        tab[k - lo] = k;
-        return;
-    }
-    unsigned s = (unsigned)k & mask;
-    while (true) {
-        int old = atomicCAS(&tab[s], kEmpty, k);
-        if (old == kEmpty) return;
-        s = (s + 1) & mask;
-    }
-}
-
-// slot holding k, or -1
-__device__ __forceinline__ int table_find(const int* tab, unsigned mask, bool direct, int lo,
-                                          int hi, int k) {
-    if (k < lo || k > hi) return -1;
-    if (direct) return (tab[k - lo] == k) ? (k - lo) : -1;
-    unsigned s = (unsigned)k & mask;
-    while (true) {
-        int v = tab[s];
-        if (v == k) return (int)s;
-        if (v == kEmpty) return -1;
-        s = (s + 1) & mask;
-    }
-}
-
-// One warp walks tasks [t0, t1) against the table.  Returns this lane's hits.
-// With PV, per-task hits go to tnew[i] and per-slot hits to slot_hits.
-template <bool PV>
-__device__ __forceinline__ uint64_t warp_probe_tasks(const Task* __restrict__ tasks, int64_t t0,
-                                                     int64_t t1, int64_t tstride,
-                                                     const int32_t* __restrict__ adj,
-                                                     const int* tab, unsigned mask, bool direct,
-                                                     int lo, int hi, unsigned* slot_hits,
-                                                     unsigned* task_hits,
-                                                     unsigned long long* tnew) {
-    const int lane = threadIdx.x & 31;
-    uint64_t hits = 0;
-    for (int64_t tb = t0; tb < t1; tb += tstride) {
-        const int64_t t = tb + lane;
-        const bool valid = t < t1;
-        int64_t start = 0;
-        int len = 0, i = 0;
-        if (valid) {
-            const Task T = tasks[t];
-            start = T.start;
-            len = T.len;
-            i = T.i;
-        }
-        const int incl = warp_incl_scan_i32(len);
-        const int excl = incl - len;
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (PV) {
-            task_hits[lane] = 0;
-            __syncwarp();
-        }
-        for (int q0 = 0; q0 < total; q0 += 32) {
-            const int q = q0 + lane;
-            // largest lane o with excl_o <= q (zero-length tasks are skipped
-            // because the next task shares their prefix)
-            int o = 0;
-#pragma unroll
-            for (int step = 16; step; step >>= 1) {
-                int c = o + step;
-                if (__shfl_sync(0xffffffffu, excl, c) <= q) o = c;
-            }
-            const int ex_o = __shfl_sync(0xffffffffu, excl, o);
-            const int64_t st_o = shfl64(start, o);
-            if (q < total) {
-                const int k = __ldg(&adj[st_o + (q - ex_o)]);
-                const int s = table_find(tab, mask, direct, lo, hi, k);
-                if (s >= 0) {
-                    ++hits;
-                    if (PV) {
-                        atomicAdd(&slot_hits[s], 1u);
-                        atomicAdd(&task_hits[o], 1u);
-                    }
-                }
-            }
-        }
-        if (PV) {
-            __syncwarp();
-            const unsigned h = task_hits[lane];
-            if (valid && h) atomicAdd(&tnew[i], (unsigned long long)h);
-            __syncwarp();
-        }
-    }
-    return hits;
-}
-
 __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
+// bits [lo, hi) of a 32-bit mask, 0 <= lo <= hi <= 32
+__device__ __forceinline__ unsigned bit_range(int lo, int hi) {
+    const unsigned up = (hi >= 32) ? 0xffffffffu : ((1u << hi) - 1u);
+    const unsigned dn = (lo >= 32) ? 0xffffffffu : ((1u << lo) - 1u);
+    return up & ~dn;
+}
+
+// ---------------------------------------------------------------------------
+// Tables for one pivot slice S = U_j[rb, re) (sorted labels lo..hi).
+//
+// Bitmap (the direct, collision-free case of Section 5.2): bit k - lo is set
+// for k in S.  Membership is one shared load and a shift.  The rank of a hit
+// among S -- its position in the slice, used to credit per-vertex counts --
+// is the 16-bit prefix popcount of the words before it plus a popcount.
+//
+// Hash (labels too spread for a bitmap): 4-slot buckets, bucket = k AND
+// (buckets - 1) (the paper's AND hash), overflow to the next bucket; the
+// occupied slots of a bucket are a prefix, so an empty last slot ends a miss.
+// Both return a counter index for per-vertex credit (rank or slot), or -1.
+// ---------------------------------------------------------------------------
+struct BitTab {
+    const unsigned* bm;
+    const unsigned short* pre;
+    int lo, hi;
+    template <bool PV>
+    __device__ __forceinline__ int find(int k) const {
+        const unsigned d = (unsigned)(k - lo);
+        if (d > (unsigned)(hi - lo)) return -1;
+        const unsigned w = bm[d >> 5];
+        if (!((w >> (d & 31)) & 1u)) return -1;
+        if (!PV) return 0;
+        return (int)pre[d >> 5] + __popc(w & ((1u << (d & 31)) - 1u));
+    }
+};
+
+struct HashTab {
+    const int* tab;
+    unsigned bmask;
+    int lo, hi;
+    template <bool PV>
+    __device__ __forceinline__ int find(int k) const {
+        if ((unsigned)(k - lo) > (unsigned)(hi - lo)) return -1;
+        unsigned b = (unsigned)k & bmask;
+        while (true) {
+            const int4 v = reinterpret_cast<const int4*>(tab)[b];
+            if (v.x == k) return (int)(4 * b);
+            if (v.y == k) return (int)(4 * b + 1);
+            if (v.z == k) return (int)(4 * b + 2);
+            if (v.w == k) return (int)(4 * b + 3);
+            if (v.w == kEmpty) return -1;
+            b = (b + 1) & bmask;
+        }
+    }
+};
+
+__device__ __forceinline__ void hash_insert(int* tab, unsigned bmask, int k) {
+    unsigned b = (unsigned)k & bmask;
+    while (true) {
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+            if (atomicCAS(&tab[4 * b + w], kEmpty, k) == kEmpty) return;
+        b = (b + 1) & bmask;
+    }
+}
+
+__device__ __forceinline__ unsigned hash_buckets(int dp) {
+    unsigned b = 1;
+    while (4 * b < 2u * (unsigned)dp) b <<= 1;   // load factor <= 1/2
+    return b;
+}
+
+// 16-bit hit counters, two per word (a counter never exceeds the tasks of a
+// unit, kept below 2^16 by the unit size cap).
+__device__ __forceinline__ void count_hit(unsigned* cnt, int r) {
+    atomicAdd(&cnt[r >> 1], 1u << ((r & 1) << 4));
+}
+__device__ __forceinline__ unsigned hit_count(const unsigned* cnt, int r) {
+    return (cnt[r >> 1] >> ((r & 1) << 4)) & 0xffffu;
+}
+
+// ---------------------------------------------------------------------------
+// One warp probes the tails of up to 32 tasks [tb, min(tb+32, t1)).
+//
+// Tails of 32 or more entries are walked one task at a time (lane p reads
+// entry p of the tail: contiguous loads, no owner lookup).  Shorter tails are
+// concatenated: lane q of a step reads entry q of the concatenation; its
+// owning task is (tasks starting at or before the step's first position) +
+// (tasks starting inside the step before q): a ballot and a warp OR-reduce.
+// Each task lane stores start - prefix, so the address is base[owner] + q.
+// PV: a task's hits are the popcounts of the hit ballots over its span, added
+// once to tnew[i]; per-entry hits go to the 16-bit counters cnt.
+// ---------------------------------------------------------------------------
+template <bool PV, class Tab>
+__device__ __forceinline__ void warp_probe_group(const Task* __restrict__ tasks, int64_t tb, int64_t t1,
+                                                 const int32_t* __restrict__ adj, const Tab& T,
+                                                 unsigned* cnt, unsigned long long* tnew,
+                                                 int64_t* s_base, uint64_t& hits, uint64_t& probes) {
+    const int lane = threadIdx.x & 31;
+    const int64_t t = tb + lane;
+    const bool valid = t < t1;
+    int64_t start = 0;
+    int len = 0, i = 0;
+    if (valid) {
+        const Task tk = tasks[t];
+        start = tk.start;
+        len = tk.len;
+        i = tk.i;
+    }
+    unsigned c = 0;
+
+    // long tails
+    unsigned longm = __ballot_sync(0xffffffffu, valid && len >= 32);
+    while (longm) {
+        const int o = __ffs(longm) - 1;
+        longm &= longm - 1;
+        const int64_t st = shfl64(start, o);
+        const int L = __shfl_sync(0xffffffffu, len, o);
+        probes += (uint64_t)L;
+        unsigned ch = 0;
+        for (int q0 = 0; q0 < L; q0 += 32 * kUnroll) {
+            int k[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int q = q0 + 32 * u + lane;
+                k[u] = (q < L) ? __ldg(&adj[st + q]) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int r = (k[u] >= 0) ? T.template find<PV>(k[u]) : -1;
+                const bool hit = r >= 0;
+                hits += hit ? 1 : 0;
+                if (PV) {
+                    ch += __popc(__ballot_sync(0xffffffffu, hit));
+                    if (hit) count_hit(cnt, r);
+                }
+            }
+        }
+        if (PV && lane == o) c += ch;
+    }
+
+    // short tails, concatenated; the short tasks' bases are compacted into
+    // s_base by rank, since the owner computed below is a rank among them
+    const int slen = (valid && len < 32) ? len : 0;
+    const int incl = warp_incl_scan_i32(slen);
+    const int excl = incl - slen;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const bool sv = slen > 0;
+    const unsigned shortm = __ballot_sync(0xffffffffu, sv);
+    const unsigned le = (2u << lane) - 1u;   // bits 0..lane
+    if (sv) s_base[__popc(shortm & (le >> 1))] = start - excl;
+    __syncwarp();
+    probes += (uint64_t)total;
+    for (int q0 = 0; q0 < total; q0 += 32 * kUnroll) {
+        int k[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int qb = q0 + 32 * u;
+            const unsigned before = __ballot_sync(0xffffffffu, sv && excl <= qb);
+            const int d = excl - qb;
+            const unsigned head = (sv && d > 0 && d < 32) ? (1u << d) : 0u;
+            const unsigned M = __reduce_or_sync(0xffffffffu, head);
+            const int o = __popc(before) - 1 + __popc(M & le);
+            const int q = qb + lane;
+            k[u] = (q < total) ? __ldg(&adj[s_base[o] + q]) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int r = (k[u] >= 0) ? T.template find<PV>(k[u]) : -1;
+            const bool hit = r >= 0;
+            hits += hit ? 1 : 0;
+            if (PV) {
+                const unsigned hm = __ballot_sync(0xffffffffu, hit);
+                const int qb = q0 + 32 * u;
+                const int plo = max(excl - qb, 0), phi = min(excl + slen - qb, 32);
+                if (sv && plo < phi) c += __popc(hm & bit_range(plo, phi));
+                if (hit) count_hit(cnt, r);
+            }
+        }
+    }
+    __syncwarp();   // s_base is rewritten by the warp's next group
+    if (PV && valid && c) atomicAdd(&tnew[i], (unsigned long long)c);
+}
+
+// ---------------------------------------------------------------------------
+// Warp units: pivots with |U_j| <= 64, one warp per unit, a private table.
+// ---------------------------------------------------------------------------
 template <class OffT, bool PV>
 __global__ void __launch_bounds__(kSmallThreads)
     k_count_small(const Unit* __restrict__ units, int64_t nunits, const Task* __restrict__ tasks,
                   const OffT* __restrict__ off, const int32_t* __restrict__ adj,
                   unsigned long long* __restrict__ ctr, unsigned long long* __restrict__ tnew) {
-    __shared__ int tab_s[kSmallWarps][kSmallTable];
-    __shared__ unsigned slot_s[kSmallWarps][PV ? kSmallTable : 1];
-    __shared__ unsigned task_s[kSmallWarps][PV ? 32 : 1];
+    __shared__ __align__(16) unsigned region_s[kSmallWarps][kSmallRegionWords];
+    __shared__ unsigned cnt_s[kSmallWarps][PV ? kSmallTable / 2 : 1];
+    __shared__ int64_t base_s[kSmallWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int* tab = tab_s[w];
-    unsigned* slot_hits = slot_s[w];
-    unsigned* task_hits = task_s[w];
-    uint64_t hits = 0;
+    unsigned* region = region_s[w];
+    unsigned* cnt = cnt_s[w];
+    uint64_t hits = 0, probes = 0, nunit = 0, ntask = 0, staged = 0;
     while (true) {
         long long u0 = 0;
         if (lane == 0) u0 = (long long)atomicAdd(&ctr[CTR_SMALL_HEAD], (unsigned long long)kGrab);
@@ -172,26 +276,77 @@ __global__ void __launch_bounds__(kSmallThreads)
             const int64_t rb = (int64_t)off[U.j], re = (int64_t)off[U.j + 1];
             const int dp = (int)(re - rb);
             const int lo = adj[rb], hi = adj[re - 1];
-            const bool direct = (int64_t)hi - lo < kSmallTable;
-            const unsigned mask = kSmallTable - 1;
-#pragma unroll
-            for (int s = lane; s < kSmallTable; s += 32) {
-                tab[s] = kEmpty;
-                if (PV) slot_hits[s] = 0;
-            }
-            __syncwarp();
-            for (int q = lane; q < dp; q += 32) table_insert(tab, mask, direct, lo, adj[rb + q]);
-            __syncwarp();
-            uint64_t uh = warp_probe_tasks<PV>(tasks, U.t0, U.t1, 32, adj, tab, mask, direct, lo, hi,
-                                               slot_hits, task_hits, tnew);
-            hits += uh;
+            const int mine = (lane < dp) ? adj[rb + lane] : 0;
+            const int mine2 = (lane + 32 < dp) ? adj[rb + 32 + lane] : 0;
+            const bool bitmap = (int64_t)hi - lo < 32 * kSmallBitWords;
+            uint64_t uh = 0;
             if (PV) {
+                for (int s = lane; s < kSmallTable / 2; s += 32) cnt[s] = 0;
+            }
+            if (bitmap) {
+                const int words = ((hi - lo) >> 5) + 1;
+                for (int s = lane; s < words; s += 32) region[s] = 0;
                 __syncwarp();
+                if (lane < dp) atomicOr(&region[(mine - lo) >> 5], 1u << ((mine - lo) & 31));
+                if (lane + 32 < dp) atomicOr(&region[(mine2 - lo) >> 5], 1u << ((mine2 - lo) & 31));
+                __syncwarp();
+                unsigned short* pre = reinterpret_cast<unsigned short*>(region + kSmallBitWords);
+                if (PV) {
+                    // prefix popcounts of the (at most 128) words, 4 per lane
+                    int a[4], sum = 0;
 #pragma unroll
-                for (int s = lane; s < kSmallTable; s += 32) {
-                    const unsigned c = slot_hits[s];
-                    if (c) atomicAdd(&tnew[tab[s]], (unsigned long long)c);
+                    for (int q = 0; q < 4; ++q) {
+                        const int wi = lane * 4 + q;
+                        a[q] = (wi < words) ? __popc(region[wi]) : 0;
+                        sum += a[q];
+                    }
+                    int run = warp_incl_scan_i32(sum) - sum;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int wi = lane * 4 + q;
+                        if (wi < words) pre[wi] = (unsigned short)run;
+                        run += a[q];
+                    }
                 }
+                __syncwarp();
+                const BitTab T{region, pre, lo, hi};
+                for (int64_t tb = U.t0; tb < U.t1; tb += 32)
+                    warp_probe_group<PV>(tasks, tb, U.t1, adj, T, cnt, tnew, base_s[w], uh, probes);
+                __syncwarp();
+                if (PV) {
+                    if (lane < dp) {
+                        const unsigned h = hit_count(cnt, lane);
+                        if (h) atomicAdd(&tnew[mine], (unsigned long long)h);
+                    }
+                    if (lane + 32 < dp) {
+                        const unsigned h = hit_count(cnt, lane + 32);
+                        if (h) atomicAdd(&tnew[mine2], (unsigned long long)h);
+                    }
+                }
+            } else {
+                int* tab = reinterpret_cast<int*>(region);
+                const unsigned bmask = hash_buckets(dp) - 1u;
+                for (int s = lane; s < kSmallTable; s += 32) tab[s] = kEmpty;
+                __syncwarp();
+                if (lane < dp) hash_insert(tab, bmask, mine);
+                if (lane + 32 < dp) hash_insert(tab, bmask, mine2);
+                __syncwarp();
+                const HashTab T{tab, bmask, lo, hi};
+                for (int64_t tb = U.t0; tb < U.t1; tb += 32)
+                    warp_probe_group<PV>(tasks, tb, U.t1, adj, T, cnt, tnew, base_s[w], uh, probes);
+                __syncwarp();
+                if (PV) {
+                    for (int s = lane; s < kSmallTable; s += 32) {
+                        const unsigned h = hit_count(cnt, s);
+                        if (h) atomicAdd(&tnew[tab[s]], (unsigned long long)h);
+                    }
+                }
+            }
+            hits += uh;
+            nunit += 1;
+            ntask += (uint64_t)(U.t1 - U.t0);
+            staged += (uint64_t)dp;
+            if (PV) {
                 uh = warp_sum_u64(uh);
                 if (lane == 0 && uh) atomicAdd(&tnew[U.j], (unsigned long long)uh);
             }
@@ -199,54 +354,130 @@ __global__ void __launch_bounds__(kSmallThreads)
         }
     }
     hits = warp_sum_u64(hits);
-    if (lane == 0 && hits) atomicAdd(&ctr[CTR_TOTAL], (unsigned long long)hits);
+    if (lane == 0) {
+        if (hits) atomicAdd(&ctr[CTR_TOTAL], (unsigned long long)hits);
+        atomicAdd(&ctr[CTR_UNITS + 0], (unsigned long long)nunit);
+        atomicAdd(&ctr[CTR_TASKS + 0], (unsigned long long)ntask);
+        atomicAdd(&ctr[CTR_PROBES + 0], (unsigned long long)probes);
+        atomicAdd(&ctr[CTR_STAGED + 0], (unsigned long long)staged);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CTA units: a slice of a larger pivot, its table shared by the CTA; warps
+// take groups of 32 tasks from a shared counter until the unit is done.
+// ---------------------------------------------------------------------------
+template <bool PV, class Tab>
+__device__ __forceinline__ void cta_probe_unit(const Task* __restrict__ tasks, const Unit& U,
+                                               const int32_t* __restrict__ adj, const Tab& T,
+                                               unsigned* cnt, unsigned long long* tnew,
+                                               int* s_next, int64_t* s_base, uint64_t& uh,
+                                               uint64_t& probes) {
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        int g = 0;
+        if (lane == 0) g = atomicAdd(s_next, 1);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        const int64_t tb = U.t0 + (int64_t)g * 32;
+        if (tb >= U.t1) break;
+        warp_probe_group<PV>(tasks, tb, U.t1, adj, T, cnt, tnew, s_base, uh, probes);
+    }
 }
 
 template <class OffT, bool PV>
-__global__ void k_count_large(const Unit* __restrict__ units, int64_t nunits,
-                              const Task* __restrict__ tasks, const OffT* __restrict__ off,
-                              const int32_t* __restrict__ adj, int slice_max,
-                              unsigned long long* __restrict__ ctr,
-                              unsigned long long* __restrict__ tnew) {
-    extern __shared__ int smem[];
+__global__ void __launch_bounds__(1024)
+    k_count_large(const Unit* __restrict__ units, int64_t nunits, const Task* __restrict__ tasks,
+                  const OffT* __restrict__ off, const int32_t* __restrict__ adj, int slice_max,
+                  unsigned long long* __restrict__ ctr, unsigned long long* __restrict__ tnew) {
+    extern __shared__ __align__(16) unsigned smem[];
     __shared__ long long s_unit;
-    __shared__ unsigned task_s[32][PV ? 32 : 1];
+    __shared__ int s_next;
     __shared__ unsigned long long s_red[32];
+    __shared__ unsigned s_wsum[32];
+    __shared__ int64_t s_base[32][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int* tab = smem;
-    uint64_t hits = 0;
+    unsigned* region = smem;
+    unsigned* cnt = smem + kRegionWords;
+    uint64_t hits = 0, probes = 0, nunit = 0, ntask = 0, staged = 0;
     while (true) {
-        if (threadIdx.x == 0) s_unit = (long long)atomicAdd(&ctr[CTR_LARGE_HEAD], 1ull);
+        if (threadIdx.x == 0) {
+            s_unit = (long long)atomicAdd(&ctr[CTR_LARGE_HEAD], 1ull);
+            s_next = 0;
+        }
         __syncthreads();
         const long long u = s_unit;
         if (u >= nunits) break;
         const Unit U = units[u];
-        const int64_t row_b = (int64_t)off[U.j], row_e = (int64_t)off[U.j + 1];
-        const int64_t rb = row_b + (int64_t)U.slice * slice_max;
-        const int64_t re = min64(row_e, rb + slice_max);
+        const int64_t rb = (int64_t)off[U.j] + (int64_t)U.slice * slice_max;
+        const int64_t re = min64((int64_t)off[U.j + 1], rb + slice_max);
         const int dp = (int)(re - rb);
-        int size = 256;
-        while (size < 2 * dp) size <<= 1;
-        const unsigned mask = (unsigned)size - 1u;
         const int lo = adj[rb], hi = adj[re - 1];
-        const bool direct = (int64_t)hi - lo < size;
-        unsigned* slot_hits = reinterpret_cast<unsigned*>(smem + size);
-        for (int s = threadIdx.x; s < size; s += blockDim.x) {
-            tab[s] = kEmpty;
-            if (PV) slot_hits[s] = 0;
-        }
-        __syncthreads();
-        for (int q = threadIdx.x; q < dp; q += blockDim.x) table_insert(tab, mask, direct, lo, adj[rb + q]);
-        __syncthreads();
-        uint64_t uh = warp_probe_tasks<PV>(tasks, U.t0 + (int64_t)w * 32, U.t1, (int64_t)nw * 32, adj,
-                                           tab, mask, direct, lo, hi, slot_hits, task_s[w], tnew);
-        hits += uh;
-        __syncthreads();
-        if (PV) {
-            for (int s = threadIdx.x; s < size; s += blockDim.x) {
-                const unsigned c = slot_hits[s];
-                if (c) atomicAdd(&tnew[tab[s]], (unsigned long long)c);
+        const bool bitmap = (int64_t)hi - lo < 32ll * kBitWords;
+        uint64_t uh = 0;
+        if (PV)
+            for (int s = threadIdx.x; s < kRegionWords / 2; s += blockDim.x) cnt[s] = 0;
+        if (bitmap) {
+            const int words = ((hi - lo) >> 5) + 1;
+            for (int s = threadIdx.x; s < words; s += blockDim.x) region[s] = 0;
+            __syncthreads();
+            for (int q = threadIdx.x; q < dp; q += blockDim.x) {
+                const int k = adj[rb + q] - lo;
+                atomicOr(&region[k >> 5], 1u << (k & 31));
             }
+            __syncthreads();
+            unsigned short* pre = reinterpret_cast<unsigned short*>(region + kBitWords);
+            if (PV) {
+                // prefix popcounts over the words: each thread a contiguous run
+                const int per = (words + blockDim.x - 1) / blockDim.x;
+                const int w0 = threadIdx.x * per;
+                int sum = 0;
+                for (int q = 0; q < per; ++q)
+                    if (w0 + q < words) sum += __popc(region[w0 + q]);
+                int inc = warp_incl_scan_i32(sum);
+                if (lane == 31) s_wsum[w] = (unsigned)inc;
+                __syncthreads();
+                int before = 0;
+                for (int q = 0; q < w; ++q) before += (int)s_wsum[q];
+                int run = before + inc - sum;
+                for (int q = 0; q < per; ++q)
+                    if (w0 + q < words) {
+                        pre[w0 + q] = (unsigned short)run;
+                        run += __popc(region[w0 + q]);
+                    }
+                __syncthreads();
+            }
+            const BitTab T{region, pre, lo, hi};
+            cta_probe_unit<PV>(tasks, U, adj, T, cnt, tnew, &s_next, s_base[w], uh, probes);
+            __syncthreads();
+            if (PV)
+                for (int r = threadIdx.x; r < dp; r += blockDim.x) {
+                    const unsigned h = hit_count(cnt, r);
+                    if (h) atomicAdd(&tnew[adj[rb + r]], (unsigned long long)h);
+                }
+        } else {
+            int* tab = reinterpret_cast<int*>(region);
+            const unsigned buckets = hash_buckets(dp);
+            const unsigned bmask = buckets - 1u;
+            for (int s = threadIdx.x; s < 4 * (int)buckets; s += blockDim.x) tab[s] = kEmpty;
+            __syncthreads();
+            for (int q = threadIdx.x; q < dp; q += blockDim.x) hash_insert(tab, bmask, adj[rb + q]);
+            __syncthreads();
+            const HashTab T{tab, bmask, lo, hi};
+            cta_probe_unit<PV>(tasks, U, adj, T, cnt, tnew, &s_next, s_base[w], uh, probes);
+            __syncthreads();
+            if (PV)
+                for (int s = threadIdx.x; s < 4 * (int)buckets; s += blockDim.x) {
+                    const unsigned h = hit_count(cnt, s);
+                    if (h) atomicAdd(&tnew[tab[s]], (unsigned long long)h);
+                }
+        }
+        hits += uh;
+        if (threadIdx.x == 0) {
+            nunit += 1;
+            ntask += (uint64_t)(U.t1 - U.t0);
+            staged += (uint64_t)dp;
+        }
+        if (PV) {
             uh = warp_sum_u64(uh);
             if (lane == 0) s_red[w] = uh;
             __syncthreads();
@@ -255,11 +486,19 @@ __global__ void k_count_large(const Unit* __restrict__ units, int64_t nunits,
                 for (int q = 0; q < nw; ++q) tot += s_red[q];
                 if (tot) atomicAdd(&tnew[U.j], tot);
             }
-            __syncthreads();
         }
+        __syncthreads();
     }
     hits = warp_sum_u64(hits);
-    if (lane == 0 && hits) atomicAdd(&ctr[CTR_TOTAL], (unsigned long long)hits);
+    if (lane == 0) {
+        if (hits) atomicAdd(&ctr[CTR_TOTAL], (unsigned long long)hits);
+        atomicAdd(&ctr[CTR_PROBES + 1], (unsigned long long)probes);
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(&ctr[CTR_UNITS + 1], (unsigned long long)nunit);
+        atomicAdd(&ctr[CTR_TASKS + 1], (unsigned long long)ntask);
+        atomicAdd(&ctr[CTR_STAGED + 1], (unsigned long long)staged);
+    }
 }
 
 __global__ void k_gather_pv(const unsigned long long* __restrict__ tnew,
@@ -366,10 +605,6 @@ void build_units_t(tc_graph* g, const tc_tuning& t, cudaStream_t st) {
     }
     g->n_small = ns;
     g->n_large = nl;
-    int size = 256;
-    const int64_t need = min64(g->stats.max_outdeg, t.slice_max);
-    while (size < 2 * need) size <<= 1;
-    g->large_table = size;
     g->units_tuning = t;
     g->stats.small_units = ns;
     g->stats.large_units = nl;
@@ -396,17 +631,17 @@ void count_t(const tc_graph* g, const tc_tuning& t, cudaStream_t st) {
     }
     if (g->n_large > 0) {
         const int threads = t.cta_threads;
-        const size_t smem = sizeof(int) * (size_t)g->large_table * (PV ? 2 : 1);
+        const size_t smem = sizeof(unsigned) * (size_t)(kRegionWords + (PV ? kRegionWords / 2 : 0));
         auto kern = k_count_large<OffT, PV>;
         TC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
         per_sm = std::max(per_sm, 1);
-        unsigned grid = (unsigned)std::max<int64_t>(1, min64((int64_t)sms * per_sm, g->n_large));
+        unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, g->n_large));
         {
             Prof prof_("k_count_large", st);
             kern<<<grid, threads, smem, st>>>(g->large_units, g->n_large, g->tasks, off, g->adj,
-                                          t.slice_max, g->counters, tnew);
+                                              t.slice_max, g->counters, tnew);
         }
         TC_LAUNCH_CHECK();
     }

@@ -63,7 +63,13 @@ _lib: Optional[ctypes.CDLL] = None
 # Every symbol include/tc.h declares (checked by the tests).
 EXPORTS = ("tc_preprocess", "tc_count", "tc_triangles", "tc_graph_get_stats", "tc_graph_free",
            "tc_tuning_default", "tc_last_error", "tc_generate_rmat", "tc_kernel_launches",
-           "tc_profile_enable", "tc_profile_read")
+           "tc_profile_enable", "tc_profile_read", "tc_count_get_stats")
+
+
+class CountStats(ctypes.Structure):
+    _fields_ = [("triangles", ctypes.c_uint64), ("units", ctypes.c_uint64 * 2),
+                ("tasks", ctypes.c_uint64 * 2), ("probes", ctypes.c_uint64 * 2),
+                ("staged", ctypes.c_uint64 * 2)]
 
 
 class KernelTime(ctypes.Structure):
@@ -98,6 +104,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tc_last_error.restype = ctypes.c_char_p
     lib.tc_generate_rmat.argtypes = [u64, i32, i64, i64, i64, u32, u32, u32, vp, vp, vp]
     lib.tc_generate_rmat.restype = st
+    lib.tc_count_get_stats.argtypes = [vp, ctypes.POINTER(CountStats), vp]
+    lib.tc_count_get_stats.restype = st
     lib.tc_kernel_launches.argtypes = []
     lib.tc_kernel_launches.restype = ctypes.c_longlong
     lib.tc_profile_enable.argtypes = [i32]
@@ -188,6 +196,13 @@ class Graph:
         _check(load().tc_graph_get_stats(self._h, ctypes.byref(s)))
         return {f: getattr(s, f) for f, _ in GraphStats._fields_ if f != "pad"}
 
+    def count_stats(self, stream=None) -> dict:
+        """Work counters of the last count (tc_count_get_stats)."""
+        c = CountStats()
+        _check(load().tc_count_get_stats(self._h, ctypes.byref(c), _stream_ptr(stream)))
+        return {"triangles": int(c.triangles), "units": list(c.units), "tasks": list(c.tasks),
+                "probes": list(c.probes), "staged": list(c.staged)}
+
     def count(self, per_vertex=None, total_dev=None, tuning: Optional[Tuning] = None,
               stream=None, sync: bool = True):
         """tc_count.  ``per_vertex``: None, True (allocate) or a CUDA uint64
@@ -232,12 +247,16 @@ def preprocess(src, dst, n: int, offsets: Optional[int] = None, stream=None,
 
 
 def triangles(src: np.ndarray, dst: np.ndarray, n: int, per_vertex: bool = False,
-              offsets: Optional[int] = None, stream=None):
-    """tc_triangles on host arrays; returns total (and per-vertex numpy)."""
+              offsets: Optional[int] = None, stream=None, out: Optional[np.ndarray] = None):
+    """tc_triangles on host arrays; returns total (and per-vertex numpy,
+    written into ``out`` -- n uint64, e.g. a pinned buffer -- when given)."""
     src = np.ascontiguousarray(src, dtype=np.int32)
     dst = np.ascontiguousarray(dst, dtype=np.int32)
     total = ctypes.c_uint64(0)
-    pv = np.zeros(max(n, 1), dtype=np.uint64) if per_vertex else None
+    pv = None
+    if per_vertex:
+        pv = out if out is not None else np.zeros(max(n, 1), dtype=np.uint64)
+        assert pv.dtype in (np.uint64, np.int64) and pv.flags["C_CONTIGUOUS"] and pv.size >= n
     flags = {None: 0, 32: TC_OFFSETS_32, 64: TC_OFFSETS_64}[offsets]
     _check(load().tc_triangles(src.ctypes.data, dst.ctypes.data, src.shape[0], n, flags,
                                _stream_ptr(stream), ctypes.addressof(total),

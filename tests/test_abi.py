@@ -54,7 +54,7 @@ def test_binding_loads_without_gpu(lib_path):
     lib = tc.load(lib_path)
     assert lib.tc_last_error() == b""
     t = tc.tuning_default()
-    assert t.small_max_outdeg == 64 and t.slice_max == 8192
+    assert t.small_max_outdeg == 64 and t.slice_max == 4096
     # argument errors are reported without touching the device
     with pytest.raises(tc.TCError) as ei:
         tc._check(lib.tc_count(None, None, None, None, None, None))
