@@ -148,22 +148,55 @@ __device__ __forceinline__ unsigned hit_count(const unsigned* cnt, int r) {
 }
 
 // ---------------------------------------------------------------------------
-// One warp probes the tails of up to 32 tasks [tb, min(tb+32, t1)).
+// One warp walks one long tail (>= 32 entries): lane p reads entry p, so the
+// loads are contiguous.  Returns the hits of this task (same in every lane).
+// ---------------------------------------------------------------------------
+template <bool PV, class Tab>
+__device__ __forceinline__ unsigned warp_walk_tail(int64_t st, int L, const int32_t* __restrict__ adj,
+                                                   const Tab& T, unsigned* cnt, uint64_t& hits) {
+    const int lane = threadIdx.x & 31;
+    unsigned ch = 0;
+    for (int q0 = 0; q0 < L; q0 += 32 * kUnroll) {
+        int k[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int q = q0 + 32 * u + lane;
+            k[u] = (q < L) ? __ldg(&adj[st + q]) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int r = (k[u] >= 0) ? T.template find<PV>(k[u]) : -1;
+            const bool hit = r >= 0;
+            hits += hit ? 1 : 0;
+            if (PV) {
+                ch += __popc(__ballot_sync(0xffffffffu, hit));
+                if (hit) count_hit(cnt, r);
+            }
+        }
+    }
+    return ch;
+}
+
+// ---------------------------------------------------------------------------
+// One warp takes up to 32 tasks [tb, min(tb+32, t1)).
 //
-// Tails of 32 or more entries are walked one task at a time (lane p reads
-// entry p of the tail: contiguous loads, no owner lookup).  Shorter tails are
-// concatenated: lane q of a step reads entry q of the concatenation; its
-// owning task is (tasks starting at or before the step's first position) +
-// (tasks starting inside the step before q): a ballot and a warp OR-reduce.
-// Each task lane stores start - prefix, so the address is base[owner] + q.
-// PV: a task's hits are the popcounts of the hit ballots over its span, added
-// once to tnew[i]; per-entry hits go to the 16-bit counters cnt.
+// Long tails (>= 32 entries) are either walked right away (defer == null) or
+// appended to the CTA's queue of long tasks (their index relative to t0), to
+// be shared out one task per warp later.  Short tails are concatenated: lane
+// q of a step reads entry q of the concatenation; its owner is the number of
+// short tasks starting at or before the step's first position, plus those
+// starting inside the step before q (a ballot and a warp OR-reduce), minus
+// one; the short tasks' start - prefix are compacted into s_base by rank, so
+// the address is s_base[owner] + q.
+// PV: a short task's hits are the popcounts of the hit ballots over its span;
+// each task's hits go once to tnew[i]; per-entry hits to the counters cnt.
 // ---------------------------------------------------------------------------
 template <bool PV, class Tab>
 __device__ __forceinline__ void warp_probe_group(const Task* __restrict__ tasks, int64_t tb, int64_t t1,
                                                  const int32_t* __restrict__ adj, const Tab& T,
                                                  unsigned* cnt, unsigned long long* tnew,
-                                                 int64_t* s_base, uint64_t& hits, uint64_t& probes) {
+                                                 int64_t* s_base, int64_t t0, unsigned short* defer,
+                                                 int* ndefer, uint64_t& hits, uint64_t& probes) {
     const int lane = threadIdx.x & 31;
     const int64_t t = tb + lane;
     const bool valid = t < t1;
@@ -176,46 +209,37 @@ __device__ __forceinline__ void warp_probe_group(const Task* __restrict__ tasks,
         i = tk.i;
     }
     unsigned c = 0;
+    const unsigned le = (2u << lane) - 1u;   // bits 0..lane
 
     // long tails
-    unsigned longm = __ballot_sync(0xffffffffu, valid && len >= 32);
-    while (longm) {
-        const int o = __ffs(longm) - 1;
-        longm &= longm - 1;
-        const int64_t st = shfl64(start, o);
-        const int L = __shfl_sync(0xffffffffu, len, o);
-        probes += (uint64_t)L;
-        unsigned ch = 0;
-        for (int q0 = 0; q0 < L; q0 += 32 * kUnroll) {
-            int k[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const int q = q0 + 32 * u + lane;
-                k[u] = (q < L) ? __ldg(&adj[st + q]) : -1;
-            }
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const int r = (k[u] >= 0) ? T.template find<PV>(k[u]) : -1;
-                const bool hit = r >= 0;
-                hits += hit ? 1 : 0;
-                if (PV) {
-                    ch += __popc(__ballot_sync(0xffffffffu, hit));
-                    if (hit) count_hit(cnt, r);
-                }
-            }
+    const bool lg = valid && len >= 32;
+    unsigned longm = __ballot_sync(0xffffffffu, lg);
+    if (defer) {
+        if (longm) {
+            int slot = 0;
+            if (lane == 0) slot = atomicAdd(ndefer, __popc(longm));
+            slot = __shfl_sync(0xffffffffu, slot, 0);
+            if (lg) defer[slot + __popc(longm & (le >> 1))] = (unsigned short)(t - t0);
         }
-        if (PV && lane == o) c += ch;
+    } else {
+        while (longm) {
+            const int o = __ffs(longm) - 1;
+            longm &= longm - 1;
+            const int64_t st = shfl64(start, o);
+            const int L = __shfl_sync(0xffffffffu, len, o);
+            probes += (uint64_t)L;
+            const unsigned ch = warp_walk_tail<PV>(st, L, adj, T, cnt, hits);
+            if (PV && lane == o) c += ch;
+        }
     }
 
-    // short tails, concatenated; the short tasks' bases are compacted into
-    // s_base by rank, since the owner computed below is a rank among them
+    // short tails, concatenated
     const int slen = (valid && len < 32) ? len : 0;
     const int incl = warp_incl_scan_i32(slen);
     const int excl = incl - slen;
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     const bool sv = slen > 0;
     const unsigned shortm = __ballot_sync(0xffffffffu, sv);
-    const unsigned le = (2u << lane) - 1u;   // bits 0..lane
     if (sv) s_base[__popc(shortm & (le >> 1))] = start - excl;
     __syncwarp();
     probes += (uint64_t)total;
@@ -311,7 +335,8 @@ __global__ void __launch_bounds__(kSmallThreads)
                 __syncwarp();
                 const BitTab T{region, pre, lo, hi};
                 for (int64_t tb = U.t0; tb < U.t1; tb += 32)
-                    warp_probe_group<PV>(tasks, tb, U.t1, adj, T, cnt, tnew, base_s[w], uh, probes);
+                    warp_probe_group<PV>(tasks, tb, U.t1, adj, T, cnt, tnew, base_s[w], U.t0,
+                                         nullptr, nullptr, uh, probes);
                 __syncwarp();
                 if (PV) {
                     if (lane < dp) {
@@ -333,7 +358,8 @@ __global__ void __launch_bounds__(kSmallThreads)
                 __syncwarp();
                 const HashTab T{tab, bmask, lo, hi};
                 for (int64_t tb = U.t0; tb < U.t1; tb += 32)
-                    warp_probe_group<PV>(tasks, tb, U.t1, adj, T, cnt, tnew, base_s[w], uh, probes);
+                    warp_probe_group<PV>(tasks, tb, U.t1, adj, T, cnt, tnew, base_s[w], U.t0,
+                                         nullptr, nullptr, uh, probes);
                 __syncwarp();
                 if (PV) {
                     for (int s = lane; s < kSmallTable; s += 32) {
@@ -371,16 +397,30 @@ template <bool PV, class Tab>
 __device__ __forceinline__ void cta_probe_unit(const Task* __restrict__ tasks, const Unit& U,
                                                const int32_t* __restrict__ adj, const Tab& T,
                                                unsigned* cnt, unsigned long long* tnew,
-                                               int* s_next, int64_t* s_base, uint64_t& uh,
-                                               uint64_t& probes) {
+                                               int* s_ctl, int64_t* s_base, unsigned short* s_long,
+                                               uint64_t& uh, uint64_t& probes) {
+    // s_ctl: [0] next group, [1] deferred long tasks, [2] next long task
     const int lane = threadIdx.x & 31;
-    while (true) {
+    while (true) {   // phase A: groups of 32 tasks, short tails, defer long ones
         int g = 0;
-        if (lane == 0) g = atomicAdd(s_next, 1);
+        if (lane == 0) g = atomicAdd(&s_ctl[0], 1);
         g = __shfl_sync(0xffffffffu, g, 0);
         const int64_t tb = U.t0 + (int64_t)g * 32;
         if (tb >= U.t1) break;
-        warp_probe_group<PV>(tasks, tb, U.t1, adj, T, cnt, tnew, s_base, uh, probes);
+        warp_probe_group<PV>(tasks, tb, U.t1, adj, T, cnt, tnew, s_base, U.t0, s_long, &s_ctl[1],
+                             uh, probes);
+    }
+    __syncthreads();
+    const int nlong = s_ctl[1];
+    while (true) {   // phase B: one long task per warp at a time
+        int x = 0;
+        if (lane == 0) x = atomicAdd(&s_ctl[2], 1);
+        x = __shfl_sync(0xffffffffu, x, 0);
+        if (x >= nlong) break;
+        const Task tk = tasks[U.t0 + s_long[x]];
+        probes += (uint64_t)tk.len;
+        const unsigned ch = warp_walk_tail<PV>(tk.start, tk.len, adj, T, cnt, uh);
+        if (PV && lane == 0 && ch) atomicAdd(&tnew[tk.i], (unsigned long long)ch);
     }
 }
 
@@ -389,20 +429,24 @@ __global__ void __launch_bounds__(1024)
     k_count_large(const Unit* __restrict__ units, int64_t nunits, const Task* __restrict__ tasks,
                   const OffT* __restrict__ off, const int32_t* __restrict__ adj, int slice_max,
                   unsigned long long* __restrict__ ctr, unsigned long long* __restrict__ tnew) {
+    // dynamic shared memory: per-warp bases | table region | counters (PV) | long-task queue
     extern __shared__ __align__(16) unsigned smem[];
     __shared__ long long s_unit;
-    __shared__ int s_next;
+    __shared__ int s_ctl[4];
     __shared__ unsigned long long s_red[32];
     __shared__ unsigned s_wsum[32];
-    __shared__ int64_t s_base[32][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    unsigned* region = smem;
-    unsigned* cnt = smem + kRegionWords;
+    int64_t* s_base = reinterpret_cast<int64_t*>(smem) + 32 * w;
+    unsigned* region = smem + 64 * nw;
+    unsigned* cnt = region + kRegionWords;
+    unsigned short* s_long = reinterpret_cast<unsigned short*>(cnt + (PV ? kRegionWords / 2 : 0));
     uint64_t hits = 0, probes = 0, nunit = 0, ntask = 0, staged = 0;
     while (true) {
         if (threadIdx.x == 0) {
             s_unit = (long long)atomicAdd(&ctr[CTR_LARGE_HEAD], 1ull);
-            s_next = 0;
+            s_ctl[0] = 0;
+            s_ctl[1] = 0;
+            s_ctl[2] = 0;
         }
         __syncthreads();
         const long long u = s_unit;
@@ -447,7 +491,7 @@ __global__ void __launch_bounds__(1024)
                 __syncthreads();
             }
             const BitTab T{region, pre, lo, hi};
-            cta_probe_unit<PV>(tasks, U, adj, T, cnt, tnew, &s_next, s_base[w], uh, probes);
+            cta_probe_unit<PV>(tasks, U, adj, T, cnt, tnew, s_ctl, s_base, s_long, uh, probes);
             __syncthreads();
             if (PV)
                 for (int r = threadIdx.x; r < dp; r += blockDim.x) {
@@ -463,7 +507,7 @@ __global__ void __launch_bounds__(1024)
             for (int q = threadIdx.x; q < dp; q += blockDim.x) hash_insert(tab, bmask, adj[rb + q]);
             __syncthreads();
             const HashTab T{tab, bmask, lo, hi};
-            cta_probe_unit<PV>(tasks, U, adj, T, cnt, tnew, &s_next, s_base[w], uh, probes);
+            cta_probe_unit<PV>(tasks, U, adj, T, cnt, tnew, s_ctl, s_base, s_long, uh, probes);
             __syncthreads();
             if (PV)
                 for (int s = threadIdx.x; s < 4 * (int)buckets; s += blockDim.x) {
@@ -631,7 +675,9 @@ void count_t(const tc_graph* g, const tc_tuning& t, cudaStream_t st) {
     }
     if (g->n_large > 0) {
         const int threads = t.cta_threads;
-        const size_t smem = sizeof(unsigned) * (size_t)(kRegionWords + (PV ? kRegionWords / 2 : 0));
+        const size_t smem = sizeof(int64_t) * 32 * (size_t)(threads / 32)
+                            + sizeof(unsigned) * (size_t)(kRegionWords + (PV ? kRegionWords / 2 : 0))
+                            + sizeof(unsigned short) * (size_t)t.cta_unit_tasks;
         auto kern = k_count_large<OffT, PV>;
         TC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;

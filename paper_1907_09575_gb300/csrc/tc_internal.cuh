@@ -7,7 +7,7 @@ namespace tc {
 constexpr int kSmallTable = 128;     // hash slots of a warp unit's table
 constexpr int kSmallMaxOutdeg = 64;  // largest pivot row a warp unit takes
 constexpr int kMaxSlice = 4096;      // largest pivot slice a CTA unit tables
-constexpr int kMaxUnitTasks = 65535; // per-entry hit counters are 16 bits
+constexpr int kMaxUnitTasks = 8192;  // 16-bit hit counters; a shared long-task queue
 
 void tuning_defaults(tc_tuning* t);
 void tuning_resolve(const tc_tuning* in, tc_tuning* out);  // fills zeros, clamps
