@@ -77,7 +77,7 @@ typedef struct {
     int32_t small_max_outdeg;  /* pivots with |U_j| <= this go to warp units (<= 64) */
     int32_t warp_unit_tasks;   /* tasks per warp unit (<= 8192) */
     int32_t cta_unit_tasks;    /* tasks per CTA unit (<= 8192) */
-    int32_t cta_threads;       /* threads per CTA of the large-pivot kernel (64..1024) */
+    int32_t cta_threads;       /* threads per CTA of the large-pivot kernel (64..256) */
     int32_t slice_max;         /* pivot entries tabled at once by one CTA (64..4096) */
     int32_t reserved[3];
 } tc_tuning;

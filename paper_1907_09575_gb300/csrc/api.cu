@@ -59,7 +59,7 @@ void tuning_resolve(const tc_tuning* in, tc_tuning* out) {
     if (in->cta_unit_tasks > 0) out->cta_unit_tasks = std::min(in->cta_unit_tasks, kMaxUnitTasks);
     if (in->cta_threads > 0) {
         int th = in->cta_threads;
-        th = std::max(64, std::min(1024, th));
+        th = std::max(64, std::min(256, th));
         out->cta_threads = (th / 32) * 32;
     }
     if (in->slice_max > 0) out->slice_max = std::max(64, std::min(in->slice_max, kMaxSlice));

@@ -32,6 +32,16 @@
 namespace tc {
 namespace {
 
+#ifndef TC_VEC_WALK
+#define TC_VEC_WALK 0          // long tails read as int4 (1) or as int (0)
+#endif
+#ifndef TC_PREFETCH
+#define TC_PREFETCH 1          // prefetch the next long task's record and tail head
+#endif
+#ifndef TC_LARGE_MINB
+#define TC_LARGE_MINB 4        // CTAs per SM the CTA kernel's registers must allow
+#endif
+
 constexpr int kSmallWarps = 8;
 constexpr int kSmallThreads = kSmallWarps * 32;
 constexpr int kGrab = 4;          // warp units popped per queue access
@@ -43,8 +53,11 @@ constexpr int kSmallBitWords = 128;
 constexpr int kSmallRegionWords = kSmallBitWords + kSmallBitWords / 2;
 // CTA unit table region (32-bit words): hash slots <= 2 * slice <= 8192, or a
 // bitmap of kBitWords words (kBitWords * 32 labels) plus 16-bit prefixes
-constexpr int kBitWords = 5120;
-constexpr int kRegionWords = 8192;
+#ifndef TC_REGION_WORDS
+#define TC_REGION_WORDS 8192
+#endif
+constexpr int kRegionWords = TC_REGION_WORDS;
+constexpr int kBitWords = (kRegionWords * 2 / 3) & ~31;
 static_assert(kBitWords + kBitWords / 2 <= kRegionWords, "bitmap + prefix fit the region");
 
 __device__ __forceinline__ int64_t shfl64(int64_t v, int src) {
@@ -148,14 +161,65 @@ __device__ __forceinline__ unsigned hit_count(const unsigned* cnt, int r) {
 }
 
 // ---------------------------------------------------------------------------
-// One warp walks one long tail (>= 32 entries): lane p reads entry p, so the
-// loads are contiguous.  Returns the hits of this task (same in every lane).
+// One warp walks one long tail (>= 32 entries) adj[st, st+L).  The 16-byte
+// aligned body is read as int4 (lane p takes entries 4p..4p+3 of a 128-entry
+// step, two steps in flight); the unaligned head and the last < 4 entries
+// (at most 6) go to lanes 0..5.  Returns the task's hits (same in all lanes).
 // ---------------------------------------------------------------------------
+constexpr int kVecUnroll = 2;
+
 template <bool PV, class Tab>
-__device__ __forceinline__ unsigned warp_walk_tail(int64_t st, int L, const int32_t* __restrict__ adj,
+__device__ __forceinline__ void probe_one(const Tab& T, int k, unsigned* cnt, unsigned& mine) {
+    const int r = T.template find<PV>(k);
+    if (r >= 0) {
+        ++mine;
+        if (PV) count_hit(cnt, r);
+    }
+}
+
+template <bool PV, class Tab>
+__device__ __forceinline__ unsigned warp_walk_tail_vec(int64_t st, int L, const int32_t* __restrict__ adj,
                                                    const Tab& T, unsigned* cnt, uint64_t& hits) {
     const int lane = threadIdx.x & 31;
-    unsigned ch = 0;
+    const int h = min((int)((4 - (st & 3)) & 3), L);        // entries before the first 16-B boundary
+    const int nchunks = (L - h) >> 2;
+    const int rest = L - h - 4 * nchunks;                    // entries after the last full chunk
+    unsigned mine = 0;
+    // head and rest: at most 3 + 3 entries
+    if (lane < h + rest) {
+        const int q = (lane < h) ? lane : (h + 4 * nchunks + (lane - h));
+        probe_one<PV>(T, __ldg(&adj[st + q]), cnt, mine);
+    }
+    const int4* body = reinterpret_cast<const int4*>(adj + st + h);
+    for (int c0 = 0; c0 < nchunks; c0 += 32 * kVecUnroll) {
+        int4 v[kVecUnroll];
+#pragma unroll
+        for (int u = 0; u < kVecUnroll; ++u) {
+            const int c = c0 + 32 * u + lane;
+            v[u] = (c < nchunks) ? __ldg(&body[c]) : make_int4(-1, -1, -1, -1);
+        }
+#pragma unroll
+        for (int u = 0; u < kVecUnroll; ++u) {
+            if (v[u].x >= 0) {
+                probe_one<PV>(T, v[u].x, cnt, mine);
+                probe_one<PV>(T, v[u].y, cnt, mine);
+                probe_one<PV>(T, v[u].z, cnt, mine);
+                probe_one<PV>(T, v[u].w, cnt, mine);
+            }
+        }
+    }
+    hits += mine;
+    if (!PV) return 0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    return mine;
+}
+
+template <bool PV, class Tab>
+__device__ __forceinline__ unsigned warp_walk_tail_scalar(int64_t st, int L, const int32_t* __restrict__ adj,
+                                                          const Tab& T, unsigned* cnt, uint64_t& hits) {
+    const int lane = threadIdx.x & 31;
+    unsigned mine = 0;
     for (int q0 = 0; q0 < L; q0 += 32 * kUnroll) {
         int k[kUnroll];
 #pragma unroll
@@ -164,17 +228,24 @@ __device__ __forceinline__ unsigned warp_walk_tail(int64_t st, int L, const int3
             k[u] = (q < L) ? __ldg(&adj[st + q]) : -1;
         }
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int r = (k[u] >= 0) ? T.template find<PV>(k[u]) : -1;
-            const bool hit = r >= 0;
-            hits += hit ? 1 : 0;
-            if (PV) {
-                ch += __popc(__ballot_sync(0xffffffffu, hit));
-                if (hit) count_hit(cnt, r);
-            }
-        }
+        for (int u = 0; u < kUnroll; ++u)
+            if (k[u] >= 0) probe_one<PV>(T, k[u], cnt, mine);
     }
-    return ch;
+    hits += mine;
+    if (!PV) return 0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    return mine;
+}
+
+template <bool PV, class Tab>
+__device__ __forceinline__ unsigned warp_walk_tail(int64_t st, int L, const int32_t* __restrict__ adj,
+                                                   const Tab& T, unsigned* cnt, uint64_t& hits) {
+#if TC_VEC_WALK
+    return warp_walk_tail_vec<PV>(st, L, adj, T, cnt, hits);
+#else
+    return warp_walk_tail_scalar<PV>(st, L, adj, T, cnt, hits);
+#endif
 }
 
 // ---------------------------------------------------------------------------
@@ -412,20 +483,36 @@ __device__ __forceinline__ void cta_probe_unit(const Task* __restrict__ tasks, c
     }
     __syncthreads();
     const int nlong = s_ctl[1];
-    while (true) {   // phase B: one long task per warp at a time
-        int x = 0;
-        if (lane == 0) x = atomicAdd(&s_ctl[2], 1);
-        x = __shfl_sync(0xffffffffu, x, 0);
-        if (x >= nlong) break;
-        const Task tk = tasks[U.t0 + s_long[x]];
-        probes += (uint64_t)tk.len;
-        const unsigned ch = warp_walk_tail<PV>(tk.start, tk.len, adj, T, cnt, uh);
-        if (PV && lane == 0 && ch) atomicAdd(&tnew[tk.i], (unsigned long long)ch);
+    // phase B: one long task per warp at a time; the next task's record is
+    // loaded, and its tail's first lines prefetched, before this one is walked
+    int x = 0;
+    if (lane == 0) x = atomicAdd(&s_ctl[2], 1);
+    x = __shfl_sync(0xffffffffu, x, 0);
+    Task cur;
+    if (x < nlong) cur = tasks[U.t0 + s_long[x]];
+    while (x < nlong) {
+        int xn = 0;
+        if (lane == 0) xn = atomicAdd(&s_ctl[2], 1);
+        xn = __shfl_sync(0xffffffffu, xn, 0);
+        Task nxt;
+        nxt.len = 0;
+        if (xn < nlong) {
+            nxt = tasks[U.t0 + s_long[xn]];
+#if TC_PREFETCH
+            if (32 * lane < nxt.len)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(adj + nxt.start + 32 * lane));
+#endif
+        }
+        probes += (uint64_t)cur.len;
+        const unsigned ch = warp_walk_tail<PV>(cur.start, cur.len, adj, T, cnt, uh);
+        if (PV && lane == 0 && ch) atomicAdd(&tnew[cur.i], (unsigned long long)ch);
+        x = xn;
+        cur = nxt;
     }
 }
 
 template <class OffT, bool PV>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(256, TC_LARGE_MINB)
     k_count_large(const Unit* __restrict__ units, int64_t nunits, const Task* __restrict__ tasks,
                   const OffT* __restrict__ off, const int32_t* __restrict__ adj, int slice_max,
                   unsigned long long* __restrict__ ctr, unsigned long long* __restrict__ tnew) {
@@ -696,23 +783,27 @@ void count_t(const tc_graph* g, const tc_tuning& t, cudaStream_t st) {
 }  // namespace
 
 void build_units(tc_graph* g, const tc_tuning& t, cudaStream_t st) {
+    tc_tuning tt = t;
+    tt.slice_max = std::min(tt.slice_max, kRegionWords / 2);
     if (g->off64)
-        build_units_t<int64_t>(g, t, st);
+        build_units_t<int64_t>(g, tt, st);
     else
-        build_units_t<int32_t>(g, t, st);
+        build_units_t<int32_t>(g, tt, st);
 }
 
 void count(const tc_graph* gc, const tc_tuning& t, uint64_t* total_dev, uint64_t* per_vertex_dev,
            cudaStream_t st) {
     tc_graph* g = const_cast<tc_graph*>(gc);   // unit lists are a cache of the tuning
-    if (!tuning_equal(t, g->units_tuning)) build_units(g, t, st);
+    tc_tuning tt = t;
+    tt.slice_max = std::min(tt.slice_max, kRegionWords / 2);   // a hashed slice needs 2 slots per entry
+    if (!tuning_equal(tt, g->units_tuning)) build_units(g, tt, st);
     const bool pv = per_vertex_dev != nullptr;
     TC_CUDA(cudaMemsetAsync(g->counters, 0, sizeof(unsigned long long) * CTR_COUNT, st));
     if (pv && g->n > 0) TC_CUDA(cudaMemsetAsync(g->tnew, 0, sizeof(uint64_t) * (size_t)g->n, st));
     if (g->off64) {
-        if (pv) count_t<int64_t, true>(g, t, st); else count_t<int64_t, false>(g, t, st);
+        if (pv) count_t<int64_t, true>(g, tt, st); else count_t<int64_t, false>(g, tt, st);
     } else {
-        if (pv) count_t<int32_t, true>(g, t, st); else count_t<int32_t, false>(g, t, st);
+        if (pv) count_t<int32_t, true>(g, tt, st); else count_t<int32_t, false>(g, tt, st);
     }
     if (pv && g->n > 0) {
         {
