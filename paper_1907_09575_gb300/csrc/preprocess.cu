@@ -156,24 +156,25 @@ __global__ void k_task_count(const uint64_t* __restrict__ keys, int64_t m, int b
     if ((threadIdx.x & 31) == 0 && my) atomicAdd(probes, my);
 }
 
+// fill[j] starts at the first task slot of pivot j and is advanced atomically.
 template <class OffT>
 __global__ void k_task_fill(const uint64_t* __restrict__ keys, int64_t m, int bits,
-                            const OffT* __restrict__ off, const int64_t* __restrict__ loff,
-                            int32_t* __restrict__ cursor, Task* __restrict__ tasks) {
+                            const OffT* __restrict__ off, unsigned long long* __restrict__ fill,
+                            Task* __restrict__ tasks) {
     const uint64_t mask = (1ull << bits) - 1ull;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t k = keys[e];
-        int64_t i = (int64_t)(k >> bits);
-        int32_t j = (int32_t)(k & mask);
-        int64_t len = (int64_t)off[i + 1] - e - 1;
+        const uint64_t k = keys[e];
+        const int64_t i = (int64_t)(k >> bits);
+        const int32_t j = (int32_t)(k & mask);
+        const int64_t len = (int64_t)off[i + 1] - e - 1;
         if (len > 0) {
-            int32_t slot = atomicAdd(&cursor[j], 1);
+            const unsigned long long slot = atomicAdd(&fill[j], 1ull);
             Task t;
             t.start = e + 1;
             t.len = (int32_t)len;
             t.i = (int32_t)i;
-            tasks[loff[j] + slot] = t;
+            tasks[slot] = t;
         }
     }
 }
@@ -366,20 +367,19 @@ void preprocess(tc_graph* g, const int32_t* src_in, const int32_t* dst_in, int64
         TC_LAUNCH_CHECK();
     }
     exclusive_scan_i32_to_i64(tcount, g->loff, n, g->loff + n, al, st);
-    TC_CUDA(cudaMemsetAsync(tcount, 0, sizeof(int32_t) * std::max<int64_t>(n, 1), st));
     if (m > 0) {
-        if (g->off64)
-            {
-                Prof prof_("k_task_fill", st);
+        Buf<unsigned long long> fill(al, (size_t)std::max<int64_t>(n, 1));
+        TC_CUDA(cudaMemcpyAsync(fill.get(), g->loff, sizeof(int64_t) * (size_t)std::max<int64_t>(n, 1),
+                                cudaMemcpyDeviceToDevice, st));
+        {
+            Prof prof_("k_task_fill", st);
+            if (g->off64)
                 k_task_fill<int64_t><<<grid_for(m, kT, G), kT, 0, st>>>(
-                keys, m, bits, static_cast<const int64_t*>(g->off), g->loff, tcount, g->tasks);
-            }
-        else
-            {
-                Prof prof_("k_task_fill", st);
+                    keys, m, bits, static_cast<const int64_t*>(g->off), fill.get(), g->tasks);
+            else
                 k_task_fill<int32_t><<<grid_for(m, kT, G), kT, 0, st>>>(
-                keys, m, bits, static_cast<const int32_t*>(g->off), g->loff, tcount, g->tasks);
-            }
+                    keys, m, bits, static_cast<const int32_t*>(g->off), fill.get(), g->tasks);
+        }
         TC_LAUNCH_CHECK();
     }
     int maxout = 0;

@@ -1,12 +1,14 @@
 // Stable LSD radix sort of 64-bit keys on a bit range, 8-bit digits.
 //
-// Per digit: (1) every tile of kTile keys histograms its digits (warp peers
-// found with __match_any_sync, so equal digits cost one shared atomic per
-// warp), written digit-major; (2) one exclusive scan over that table gives
-// each (digit, tile) its global output offset; (3) every tile ranks its keys
-// stably (warp w owns a contiguous segment, ranks come from match_any peer
-// masks plus a running per-warp counter), permutes them into digit order in
-// shared memory and writes each digit run out contiguously.
+// Per digit: (1) every tile of kTile keys counts its digits into per-warp
+// shared histograms (plain shared atomics; a warp whose keys all share one
+// digit adds once), written digit-major to the (digit, tile) table; (2) one
+// exclusive scan of that table gives each (digit, tile) its output offset;
+// (3) every tile loads its keys into shared memory, ranks them stably (warp w
+// owns a contiguous segment; the lanes holding the same digit are found with
+// one ballot per digit bit, and a running per-warp counter orders the
+// rounds), permutes them into digit order in shared memory and writes each
+// digit run out contiguously.
 #include "common.cuh"
 
 namespace tc {
@@ -32,14 +34,23 @@ __global__ void __launch_bounds__(kThreads) k_hist(const uint64_t* __restrict__ 
     for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&hist[0][0])[i] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)w * kSeg;
-#pragma unroll 4
+    uint64_t k[kRounds];
+#pragma unroll
     for (int r = 0; r < kRounds; ++r) {
-        int64_t idx = base + r * 32 + lane;
-        bool valid = idx < count;
-        unsigned d = valid ? digit_of(keys[idx], shift, mask) : (kRadix + lane);
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        int leader = __ffs(peers) - 1;
-        if (valid && lane == leader) hist[w][d] += __popc(peers);
+        const int64_t idx = base + r * 32 + lane;
+        k[r] = idx < count ? keys[idx] : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const bool valid = base + r * 32 + lane < count;
+        const unsigned d = digit_of(k[r], shift, mask);
+        const unsigned d0 = __shfl_sync(0xffffffffu, d, 0);
+        const unsigned vm = __ballot_sync(0xffffffffu, valid);
+        if (__all_sync(0xffffffffu, !valid || d == d0)) {
+            if (lane == 0 && vm) atomicAdd(&hist[w][d0], (unsigned)__popc(vm));
+        } else if (valid) {
+            atomicAdd(&hist[w][d], 1u);
+        }
     }
     __syncthreads();
     for (int d = threadIdx.x; d <= (int)mask; d += kThreads) {
@@ -50,78 +61,112 @@ __global__ void __launch_bounds__(kThreads) k_hist(const uint64_t* __restrict__ 
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_scatter(const uint64_t* __restrict__ in,
-                                                      uint64_t* __restrict__ out, int64_t count,
-                                                      int shift, unsigned mask,
-                                                      const int64_t* __restrict__ H,
-                                                      int64_t nblocks) {
+// Lanes of the warp whose digit equals this lane's (one ballot per digit bit).
+__device__ __forceinline__ unsigned digit_peers(unsigned d, int nbits, unsigned valid_mask) {
+    unsigned peers = valid_mask;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        if (b < nbits) {
+            const bool bit = (d >> b) & 1u;
+            const unsigned bal = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? bal : ~bal;
+        }
+    }
+    return peers;
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_scatter(const uint64_t* __restrict__ in,
+                                                         uint64_t* __restrict__ out, int64_t count,
+                                                         int shift, int nbits,
+                                                         const int64_t* __restrict__ H,
+                                                         int64_t nblocks) {
     __shared__ uint64_t stage[kTile];
-    __shared__ unsigned wcnt[kWarps][kRadix];   // counts, then per-warp exclusive prefix
-    __shared__ unsigned dstart[kRadix];         // tile-local start of each digit run
+    __shared__ unsigned short rank_s[kTile];
+    __shared__ unsigned short wcnt[kWarps][kRadix];   // counts, then per-warp exclusive prefix
+    __shared__ unsigned dstart[kRadix];               // tile-local start of each digit run
     __shared__ unsigned wsum[kWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
+    const unsigned mask = (1u << nbits) - 1u;
+    const int64_t tbase = (int64_t)blockIdx.x * kTile;
+    const int valid_in_tile = (int)min64((int64_t)kTile, count - tbase);
+
     for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&wcnt[0][0])[i] = 0;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const int p = k * kThreads + threadIdx.x;
+        if (p < valid_in_tile) stage[p] = in[tbase + p];
+    }
     __syncthreads();
 
-    const int64_t tbase = (int64_t)blockIdx.x * kTile;
-    const int64_t base = tbase + (int64_t)w * kSeg;
-    uint64_t key[kRounds];
-    unsigned rank[kRounds];
-#pragma unroll
+    // stable ranks within each warp's segment
+    const int seg = w * kSeg;
+#pragma unroll 4
     for (int r = 0; r < kRounds; ++r) {
-        int64_t idx = base + r * 32 + lane;
-        bool valid = idx < count;
-        key[r] = valid ? in[idx] : 0;
-        unsigned d = valid ? digit_of(key[r], shift, mask) : (kRadix + lane);
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        unsigned prior = valid ? wcnt[w][d] : 0;
+        const int p = seg + r * 32 + lane;
+        const bool valid = p < valid_in_tile;
+        const unsigned vm = __ballot_sync(0xffffffffu, valid);
+        const unsigned d = valid ? digit_of(stage[p], shift, mask) : 0u;
+        const unsigned peers = digit_peers(d, nbits, vm);
+        const unsigned prior = valid ? wcnt[w][d] : 0u;
         __syncwarp();
-        rank[r] = prior + __popc(peers & lt);
-        if (valid && lane == __ffs(peers) - 1) wcnt[w][d] = prior + __popc(peers);
+        if (valid) {
+            rank_s[p] = (unsigned short)(prior + __popc(peers & lt));
+            if (lane == __ffs(peers) - 1) wcnt[w][d] = (unsigned short)(prior + __popc(peers));
+        }
         __syncwarp();
     }
     __syncthreads();
     // per-warp exclusive prefix per digit, and digit totals
     unsigned tot = 0;
-    if (threadIdx.x < kRadix) {
-        const int d = threadIdx.x;
+    {
+        const int d = threadIdx.x;   // kThreads == kRadix
 #pragma unroll
         for (int q = 0; q < kWarps; ++q) {
-            unsigned c = wcnt[q][d];
-            wcnt[q][d] = tot;
+            const unsigned c = wcnt[q][d];
+            wcnt[q][d] = (unsigned short)tot;
             tot += c;
         }
     }
-    // exclusive scan of the 256 digit totals (one per thread)
     unsigned inc = tot;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += y;
     }
     if (lane == 31) wsum[w] = inc;
     __syncthreads();
     unsigned before = 0;
     for (int q = 0; q < w; ++q) before += wsum[q];
-    if (threadIdx.x < kRadix) dstart[threadIdx.x] = before + inc - tot;
+    dstart[threadIdx.x] = before + inc - tot;
     __syncthreads();
     // permute into digit order inside the tile
+    uint64_t key[kItems];
+    unsigned pos[kItems];
 #pragma unroll
-    for (int r = 0; r < kRounds; ++r) {
-        int64_t idx = base + r * 32 + lane;
-        if (idx < count) {
-            unsigned d = digit_of(key[r], shift, mask);
-            stage[dstart[d] + wcnt[w][d] + rank[r]] = key[r];
+    for (int k = 0; k < kItems; ++k) {
+        const int p = k * kThreads + threadIdx.x;
+        if (p < valid_in_tile) {
+            key[k] = stage[p];
+            const unsigned d = digit_of(key[k], shift, mask);
+            pos[k] = dstart[d] + wcnt[p / kSeg][d] + rank_s[p];
         }
     }
     __syncthreads();
-    const int valid_in_tile = (int)min64((int64_t)kTile, count - tbase);
-    for (int p = threadIdx.x; p < valid_in_tile; p += kThreads) {
-        uint64_t k = stage[p];
-        unsigned d = digit_of(k, shift, mask);
-        int64_t g = H[(int64_t)d * nblocks + blockIdx.x] + (p - (int)dstart[d]);
-        out[g] = k;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const int p = k * kThreads + threadIdx.x;
+        if (p < valid_in_tile) stage[pos[k]] = key[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        const int p = k * kThreads + threadIdx.x;
+        if (p < valid_in_tile) {
+            const uint64_t kk = stage[p];
+            const unsigned d = digit_of(kk, shift, mask);
+            out[H[(int64_t)d * nblocks + blockIdx.x] + (p - (int)dstart[d])] = kk;
+        }
     }
 }
 
@@ -144,8 +189,8 @@ void radix_sort_u64(uint64_t** keys, uint64_t** alt, int64_t count, int lo, int 
         exclusive_scan_i64(H.get(), H.get(), rows, nullptr, al, st);
         {
             Prof prof_("k_scatter", st);
-            k_scatter<<<(unsigned)nblocks, kThreads, 0, st>>>(*keys, *alt, count, shift, mask, H.get(),
-                                                          nblocks);
+            k_scatter<<<(unsigned)nblocks, kThreads, 0, st>>>(*keys, *alt, count, shift, nbits, H.get(),
+                                                              nblocks);
         }
         TC_LAUNCH_CHECK();
         uint64_t* t = *keys;
