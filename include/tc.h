@@ -201,6 +201,39 @@ TC_API tc_status tc_generate_rmat(uint64_t seed, int32_t scale, int64_t n, int64
                            int32_t* src_dev, int32_t* dst_dev, void* stream);
 
 /*
+ * tc_triangles_static -- tc_preprocess + tc_count for a small graph with no
+ * device allocation.  (The paper has no counterpart: this serves callers
+ * that cannot call cudaMalloc when they need a count, e.g. code running
+ * after start-up has given all device memory to another allocator, such as
+ * a framework's caching pool or a serving runtime with a fixed budget, or
+ * latency-critical loops that must not allocate at steady state.)
+ *
+ * Every buffer comes from one file-scope device array of 32 MiB that each
+ * GPU loading the library holds until the process exits.  The first call on
+ * a device looks up that array's address (cudaGetSymbolAddress, with the
+ * device current); make that first call before any stream capture.  Each
+ * call reuses the whole array; calls whose GPU work overlaps race on it, so
+ * issue them on one stream or synchronise between them.
+ *
+ *   src_dev, dst_dev  num_pairs device int32 ids in [0, n) (read only).
+ *   num_pairs  0 .. TC_STATIC_MAX_PAIRS.   n  0 .. TC_STATIC_MAX_VERTICES.
+ *   total_dev  device uint64 receiving the total (required).
+ *   per_vertex_dev  NULL or n device uint64 (original ids), as tc_count.
+ *   stream     cudaStream_t as void*; the call synchronises it while
+ *              preprocessing; the count itself is stream ordered.
+ *
+ * Errors: TC_EINVAL for sizes beyond the limits (with a message naming
+ * them), negative sizes, NULL required pointers or ids outside [0, n);
+ * TC_ECUDA.  Allocates nothing: no cudaMalloc, cudaFree or allocating
+ * library routine is called.
+ */
+#define TC_STATIC_MAX_PAIRS 262144
+#define TC_STATIC_MAX_VERTICES 65536
+TC_API tc_status tc_triangles_static(const int32_t* src_dev, const int32_t* dst_dev,
+                                     int64_t num_pairs, int64_t n, uint64_t* total_dev,
+                                     uint64_t* per_vertex_dev, void* stream);
+
+/*
  * Kernel accounting (not part of the paper's method; measurement support).
  *
  * tc_kernel_launches: number of kernels this library has launched since it

@@ -63,7 +63,10 @@ _lib: Optional[ctypes.CDLL] = None
 # Every symbol include/tc.h declares (checked by the tests).
 EXPORTS = ("tc_preprocess", "tc_count", "tc_triangles", "tc_graph_get_stats", "tc_graph_free",
            "tc_tuning_default", "tc_last_error", "tc_generate_rmat", "tc_kernel_launches",
-           "tc_profile_enable", "tc_profile_read", "tc_count_get_stats")
+           "tc_profile_enable", "tc_profile_read", "tc_count_get_stats", "tc_triangles_static")
+
+TC_STATIC_MAX_PAIRS = 262144
+TC_STATIC_MAX_VERTICES = 65536
 
 
 class CountStats(ctypes.Structure):
@@ -106,6 +109,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tc_generate_rmat.restype = st
     lib.tc_count_get_stats.argtypes = [vp, ctypes.POINTER(CountStats), vp]
     lib.tc_count_get_stats.restype = st
+    lib.tc_triangles_static.argtypes = [vp, vp, i64, i64, vp, vp, vp]
+    lib.tc_triangles_static.restype = st
     lib.tc_kernel_launches.argtypes = []
     lib.tc_kernel_launches.restype = ctypes.c_longlong
     lib.tc_profile_enable.argtypes = [i32]
@@ -264,6 +269,23 @@ def triangles(src: np.ndarray, dst: np.ndarray, n: int, per_vertex: bool = False
     if per_vertex:
         return int(total.value), pv[:n]
     return int(total.value)
+
+
+def triangles_static(src, dst, n: int, per_vertex=None, stream=None) -> int:
+    """tc_triangles_static: count a small graph whose pairs are CUDA int32
+    tensors without any device allocation by the library (buffers come from
+    its fixed static scratch; see include/tc.h for the limits and the rules
+    on overlapping calls).  ``per_vertex``: None or a CUDA int64 tensor of n
+    entries that receives the per-vertex counts.  Returns the total."""
+    import torch
+    ps, dev_s = _ptr(src)
+    pd, dev_d = _ptr(dst)
+    assert dev_s and dev_d, "tc_triangles_static takes device pairs"
+    total = torch.zeros(1, dtype=torch.int64, device=src.device)
+    _check(load().tc_triangles_static(ps, pd, int(src.shape[0]), n, total.data_ptr(),
+                                      per_vertex.data_ptr() if per_vertex is not None else None,
+                                      _stream_ptr(stream)))
+    return int(total.item())
 
 
 def generate_rmat(seed: int, scale: int, num_pairs: int, n: Optional[int] = None, e0: int = 0,
