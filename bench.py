@@ -49,6 +49,11 @@ WORKLOADS = {
                     desc="Chung-Lu power law, 50,000,000 vertices, exponent 2.1, mean expected "
                          "degree 40 (10^9 pairs), expected degree capped at 10^6; int64 offsets; "
                          "total count"),
+    "batch4096": dict(kind="batch", graphs=4096, offsets=32, per_vertex=False,
+                      desc="4096 independent graphs, even ids G(n,p), odd ids RMAT "
+                           "(a/b/c/d=0.57/0.19/0.19/0.05, ids >= n redrawn), n = floor(2^(8+8U)), "
+                           "mean degree 4+60U; int32 ids and offsets; one uint64 count per graph; "
+                           "autotuned unit knobs"),
 }
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
@@ -69,6 +74,8 @@ def parse():
                     help="RMAT scale of the oracle's bounded sample")
     ap.add_argument("--scale", type=int, default=None,
                     help="override the RMAT scale of the workload (small profiling cases)")
+    ap.add_argument("--graphs", type=int, default=None,
+                    help="override the number of graphs of the batch workload")
     return ap.parse_args()
 
 
@@ -433,6 +440,180 @@ def run_ours(args, wl):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------
+# batched form: many graphs, one persistent launch
+# ----------------------------------------------------------------------------
+
+def run_batch(args, wl):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1907_09575_gb300 import inputs, tc
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    tc.load()
+    ngraphs = args.graphs or wl["graphs"]
+    seed = args.seed + rank
+    t0 = time.perf_counter()
+    graphs, pairs, ms_list = [], 0, []
+    host_pairs = []   # kept pinned for the end-to-end pass
+    for k in range(ngraphs):
+        spec = inputs.batch_member(seed, k)
+        hs, hd = spec.generate()
+        pairs += hs.size
+        if not args.no_e2e:
+            ps = torch.from_numpy(hs).pin_memory()
+            pd = torch.from_numpy(hd).pin_memory()
+            host_pairs.append((ps, pd, spec.n))
+        graphs.append(tc.preprocess(torch.from_numpy(hs).cuda(), torch.from_numpy(hd).cuda(),
+                                    spec.n, offsets=wl["offsets"]))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    facts = [g.stats() for g in graphs]
+    m_all = float(sum(f["m"] for f in facts))
+
+    b = tc.Batch(graphs)
+    t0 = time.perf_counter()
+    tuning = b.autotune(reps=2)
+    tune_s = time.perf_counter() - t0
+    totals = torch.zeros(ngraphs, dtype=torch.int64, device="cuda")
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):
+        b.count(totals)
+    torch.cuda.synchronize()
+    want = totals.clone()
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    tc.profile_enable(True)
+    l0 = tc.kernel_launches()
+    ev0.record()
+    for _ in range(args.steps):
+        b.count(totals)
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier()
+    launches = tc.kernel_launches() - l0
+    prof = tc.profile_read()
+    tc.profile_enable(False)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    kst = b.count_stats()
+    assert torch.equal(totals, want)
+
+    # the same kernel, one graph per launch, same tuning
+    per = torch.zeros(ngraphs, dtype=torch.int64, device="cuda")
+    for _ in range(max(1, args.warmup)):
+        for k, g in enumerate(graphs):
+            g.count(total_dev=per[k:k + 1], tuning=tuning, sync=False)
+    torch.cuda.synchronize()
+    tc.profile_enable(True)
+    ev0.record()
+    for _ in range(args.steps):
+        for k, g in enumerate(graphs):
+            g.count(total_dev=per[k:k + 1], tuning=tuning, sync=False)
+    ev1.record()
+    torch.cuda.synchronize()
+    pprof = tc.profile_read()
+    tc.profile_enable(False)
+    ms_one = ev0.elapsed_time(ev1) / args.steps
+    assert torch.equal(per, totals), "one-per-launch totals differ from the batch"
+
+    tt = torch.tensor([ms, ms_one, m_all], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(tt[:2], op=dist.ReduceOp.MAX)
+        msum = tt[2:].clone()
+        dist.all_reduce(msum, op=dist.ReduceOp.SUM)
+        tt[2] = msum[0]
+    ms, ms_one, m_tot = float(tt[0]), float(tt[1]), float(tt[2])
+    value = m_tot / (ms / 1e3)
+
+    hbm, peak_src = peaks()
+    kb = prof.get("k_count_batch", (args.steps, ms * args.steps))
+    b_launch = (sum(kst["units"]) * 40 + 4 * sum(kst["staged"]) + 16 * sum(kst["tasks"])
+                + 4 * sum(kst["probes"]))
+    achieved = b_launch / (kb[1] / kb[0] / 1e3) / 1e9
+    roof = {"kernel": "k_count (batched, one captured launch)", "bound": "hbm",
+            "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "traffic_note": "no ncu capture of the batched launch committed",
+            "peak_source": peak_src, "alg_bytes_per_launch": b_launch,
+            "avg_launch_ms": kb[1] / kb[0]}
+
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(max(1, min(args.steps, 2))):
+            gs2 = [tc.preprocess(ps.numpy(), pd.numpy(), n, offsets=wl["offsets"])
+                   for ps, pd, n in host_pairs]
+            out = tc.count_batch(gs2, tuning=tuning)
+            host_totals = out.cpu()
+            for g in gs2:
+                g.free()
+        e2e_s = (time.perf_counter() - t0) / max(1, min(args.steps, 2))
+        assert torch.equal(host_totals.cuda(), totals)
+        e2e = {"value": m_tot / e2e_s, "unit": "edges/s", "ms_per_step": e2e_s * 1e3,
+               "h2d_bytes_per_step": 8 * pairs, "d2h_bytes_per_step": 8 * ngraphs,
+               "call": "tc_preprocess per graph from pinned host pairs, tc_count_batch, totals to host"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        mm, k = 0, 0
+        while time.perf_counter() - t0 < 10.0 and k < ngraphs:
+            hs, hd = inputs.batch_member(seed, k).generate()
+            tot, st = oracle.count(hs, hd, inputs.batch_member(seed, k).n, stats=True)
+            assert tot == int(totals[k])
+            mm += st["m"]
+            k += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": mm / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
+               "sample": f"the first {k} graphs of the batch (m={mm}), oracle preprocess+count, "
+                         f"single thread, {dt:.1f} s (includes host generation)"}
+    if ws > 1:
+        dist.barrier()
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": "undirected edges/sec (exact triangle count, 4096-graph batch, count step)",
+        "value": value, "unit": "edges/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32 ids / uint64 counts",
+        "data": "synthetic (host-generated seeded G(n,p) and RMAT graphs)",
+        "config": {"workload": args.workload, "desc": wl["desc"], "graphs": ngraphs,
+                   "pairs": pairs, "m": int(m_tot), "seed": args.seed,
+                   "l2": f"inputs larger than L2 (CSRs and task lists of {ngraphs} graphs)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "triangles": int(totals.sum().item()),
+        "one_per_launch": {"value": m_tot / (ms_one / 1e3), "unit": "edges/s", "ms": ms_one,
+                           "launches_per_step": sum(v[0] for v in pprof.values()) // max(args.steps, 1)},
+        "batch_speedup": ms_one / ms,
+        "tuning": {f: getattr(tuning, f) for f in ("small_max_outdeg", "warp_unit_tasks",
+                                                   "cta_unit_tasks", "cta_threads", "slice_max")},
+        "autotune_s": tune_s, "setup_s": setup_s,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks, "count_work": kst,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     wl = dict(WORKLOADS[args.workload])
@@ -443,6 +624,8 @@ def main():
         args.workload = f"{args.workload}@scale{args.scale}"
     if args.impl == "reference":
         run_reference(args, wl)
+    elif wl["kind"] == "batch":
+        run_batch(args, wl)
     else:
         run_ours(args, wl)
 

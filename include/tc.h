@@ -201,6 +201,38 @@ TC_API tc_status tc_generate_rmat(uint64_t seed, int32_t scale, int64_t n, int64
                            int32_t* src_dev, int32_t* dst_dev, void* stream);
 
 /*
+ * Batched counting (no counterpart in the paper: many independent graphs
+ * counted by one persistent launch).  A batch references its graphs' arenas:
+ * they must stay alive, unchanged, until tc_batch_free.  The batch owns a
+ * view table, merged work units over all graphs and a captured CUDA graph
+ * (two memsets and the count kernel), replayed by tc_batch_count.
+ *
+ * tc_batch_create: graphs = num graph handles (num >= 1); tune NULL for
+ *   defaults; stream unused (the batch works on a private stream and
+ *   synchronises it).  *out receives the batch.  TC_EINVAL on NULL or
+ *   num <= 0; TC_ENOMEM; TC_ECUDA.
+ * tc_batch_count: one graph launch on `stream`; if totals_dev is non-NULL it
+ *   receives num device uint64 totals, in the order the graphs were given.
+ *   Stream ordered; one count at a time per batch.
+ * tc_batch_autotune: times candidate tunings (reps replays each) and keeps
+ *   the fastest; the choice is cached per degree profile (graph count, mean
+ *   edges, largest pivot row, mean tail length) for later batches in the
+ *   process.  *chosen (may be NULL) receives it.  Synchronises `stream`.
+ * tc_batch_get_count_stats: work counters of the last tc_batch_count;
+ *   triangles = sum of the totals.  Synchronises `stream`.
+ * tc_count_batch: create, count into totals_dev (required), free.
+ */
+typedef struct tc_batch tc_batch;
+TC_API tc_status tc_batch_create(const tc_graph* const* graphs, int32_t num, const tc_tuning* tune,
+                                 void* stream, tc_batch** out);
+TC_API tc_status tc_batch_count(tc_batch* b, uint64_t* totals_dev, void* stream);
+TC_API tc_status tc_batch_autotune(tc_batch* b, int32_t reps, tc_tuning* chosen, void* stream);
+TC_API tc_status tc_batch_get_count_stats(const tc_batch* b, tc_count_stats* out, void* stream);
+TC_API void tc_batch_free(tc_batch* b);
+TC_API tc_status tc_count_batch(const tc_graph* const* graphs, int32_t num, const tc_tuning* tune,
+                                uint64_t* totals_dev, void* stream);
+
+/*
  * tc_triangles_static -- tc_preprocess + tc_count for a small graph with no
  * device allocation.  (The paper has no counterpart: this serves callers
  * that cannot call cudaMalloc when they need a count, e.g. code running

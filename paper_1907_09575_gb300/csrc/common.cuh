@@ -155,6 +155,7 @@ struct tc_graph {
     struct Unit* small_units = nullptr;
     struct Unit* large_units = nullptr;
     unsigned long long* counters = nullptr;  // queue heads and totals (device)
+    struct GraphView* view = nullptr;        // device copy of this graph's view
     uint64_t* tnew = nullptr;   // per-vertex accumulator in new labels, n
 
     int64_t n_tasks = 0, n_small = 0, n_large = 0;
@@ -171,13 +172,28 @@ struct Task {
     int32_t i;       // row (new label), for per-vertex credit
 };
 
-// A work unit: pivot j, a slice of U_j (for pivots larger than one table) and
-// a contiguous range of j's tasks.
+// A work unit: graph g (index into the view table), pivot j, a slice of U_j
+// (for pivots larger than one table) and a contiguous range of j's tasks.
 struct Unit {
     int32_t j;
     int32_t slice;      // slice index of U_j (entries [slice*S, slice*S+S))
+    int32_t g;
+    int32_t pad;
     int64_t t0;         // first task (index into tasks)
     int64_t t1;         // one past the last task
+};
+
+// What the count kernel needs of one graph.
+struct GraphView {
+    const void* off;              // U offsets (int32 or int64)
+    const int32_t* adj;           // U columns
+    const int64_t* loff;          // task offsets per pivot
+    const Task* tasks;
+    unsigned long long* tnew;     // per-vertex accumulator (new labels), or null
+    unsigned long long* total;    // where this graph's hits are added
+    int64_t n;
+    int32_t off64;
+    int32_t pad;
 };
 
 // Device counters of one count: queue heads, the total, and work done by the

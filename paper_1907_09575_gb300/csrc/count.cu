@@ -7,23 +7,20 @@
 // (Eq. 1 sums exactly the k > j with u_ik = u_jk = 1).
 //
 // Tables (Section 5.2, "Modifying the hashing routine for sparser vertices"):
-// when the label span of U_j fits the table, slot = k - min(U_j) (direct, no
-// probing); otherwise slot = k AND (size-1) with linear probing, size >= 2|U_j|.
-// Probes outside [min U_j, max U_j] are rejected before the lookup, the
-// per-probe form of the early exit of Section 5.2.
+// a bitmap over [min U_j, max U_j] when that label span fits (collision
+// free), else buckets of 4 slots with bucket = k AND (buckets - 1).  Probes
+// outside [min U_j, max U_j] are rejected before the lookup, the per-probe
+// form of the early exit of Section 5.2.
 //
-// Work: units (pivot, slice of U_j, range of tasks) in two lists.  Pivots
-// with |U_j| <= 64 are handled by one warp each (a 128-slot table per warp);
-// larger pivots by one CTA with a table of up to 2 x 8192 slots, split into
-// slices beyond that.  Persistent CTAs pop units from atomic queue heads.
-// Inside a unit, a warp takes 32 tasks at a time and walks the concatenation
-// of their tails 32 probes per step (the owning task of each probe is found
-// by a 5-step shuffle binary search over the warp's prefix sums), so loads of
-// a tail are contiguous across lanes whatever the tail lengths.
+// Work: units (graph, pivot, slice of U_j, range of tasks).  Pivots with
+// |U_j| <= 64 become warp units (a private table per warp); larger ones CTA
+// units (a shared table, slices of <= 4096 entries).  One persistent kernel
+// pops CTA units first, heaviest pivots first, then warp units; units may
+// come from many graphs at once (the batched form), each graph reached
+// through a view table.
 //
-// Per-vertex counts (t[v] = triangles through v): each hit credits k through
-// a shared counter per table slot, i through a per-task shared counter, and j
-// once per unit; all flushed with one global atomic per nonzero counter.
+// Per-vertex counts (t[v] = triangles through v): a task's hits credit i once,
+// per-entry hit counters credit k once per unit, j is credited once per unit.
 #include <algorithm>
 
 #include "common.cuh"
@@ -345,150 +342,147 @@ __device__ __forceinline__ void warp_probe_group(const Task* __restrict__ tasks,
     if (PV && valid && c) atomicAdd(&tnew[i], (unsigned long long)c);
 }
 
+__device__ __forceinline__ int64_t off_at(const GraphView& G, int64_t v) {
+    return G.off64 ? static_cast<const int64_t*>(G.off)[v]
+                   : (int64_t) static_cast<const int32_t*>(G.off)[v];
+}
+
+// Per-warp running total of one graph's hits, flushed to that graph's total
+// when the warp moves to a unit of another graph (and at the end).
+struct GraphAcc {
+    int g = -1;
+    uint64_t hits = 0;
+    __device__ __forceinline__ void to(int ng, const GraphView* __restrict__ views) {
+        if (ng == g) return;
+        flush(views);
+        g = ng;
+    }
+    __device__ __forceinline__ void flush(const GraphView* __restrict__ views) {
+        const uint64_t s = warp_sum_u64(hits);
+        if ((threadIdx.x & 31) == 0 && g >= 0 && s) atomicAdd(views[g].total, (unsigned long long)s);
+        hits = 0;
+    }
+};
+
 // ---------------------------------------------------------------------------
-// Warp units: pivots with |U_j| <= 64, one warp per unit, a private table.
+// Warp unit: a pivot with |U_j| <= 64 processed by one warp with a private
+// table (a bitmap of <= 4096 labels, or 128 hash slots).
 // ---------------------------------------------------------------------------
-template <class OffT, bool PV>
-__global__ void __launch_bounds__(kSmallThreads)
-    k_count_small(const Unit* __restrict__ units, int64_t nunits, const Task* __restrict__ tasks,
-                  const OffT* __restrict__ off, const int32_t* __restrict__ adj,
-                  unsigned long long* __restrict__ ctr, unsigned long long* __restrict__ tnew) {
-    __shared__ __align__(16) unsigned region_s[kSmallWarps][kSmallRegionWords];
-    __shared__ unsigned cnt_s[kSmallWarps][PV ? kSmallTable / 2 : 1];
-    __shared__ int64_t base_s[kSmallWarps][32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    unsigned* region = region_s[w];
-    unsigned* cnt = cnt_s[w];
-    uint64_t hits = 0, probes = 0, nunit = 0, ntask = 0, staged = 0;
-    while (true) {
-        long long u0 = 0;
-        if (lane == 0) u0 = (long long)atomicAdd(&ctr[CTR_SMALL_HEAD], (unsigned long long)kGrab);
-        u0 = __shfl_sync(0xffffffffu, u0, 0);
-        if (u0 >= nunits) break;
-        const int64_t u1 = min64(u0 + kGrab, nunits);
-        for (int64_t u = u0; u < u1; ++u) {
-            const Unit U = units[u];
-            const int64_t rb = (int64_t)off[U.j], re = (int64_t)off[U.j + 1];
-            const int dp = (int)(re - rb);
-            const int lo = adj[rb], hi = adj[re - 1];
-            const int mine = (lane < dp) ? adj[rb + lane] : 0;
-            const int mine2 = (lane + 32 < dp) ? adj[rb + 32 + lane] : 0;
-            const bool bitmap = (int64_t)hi - lo < 32 * kSmallBitWords;
-            uint64_t uh = 0;
-            if (PV) {
-                for (int s = lane; s < kSmallTable / 2; s += 32) cnt[s] = 0;
-            }
-            if (bitmap) {
-                const int words = ((hi - lo) >> 5) + 1;
-                for (int s = lane; s < words; s += 32) region[s] = 0;
-                __syncwarp();
-                if (lane < dp) atomicOr(&region[(mine - lo) >> 5], 1u << ((mine - lo) & 31));
-                if (lane + 32 < dp) atomicOr(&region[(mine2 - lo) >> 5], 1u << ((mine2 - lo) & 31));
-                __syncwarp();
-                unsigned short* pre = reinterpret_cast<unsigned short*>(region + kSmallBitWords);
-                if (PV) {
-                    // prefix popcounts of the (at most 128) words, 4 per lane
-                    int a[4], sum = 0;
+template <bool PV>
+__device__ __forceinline__ void warp_unit(const GraphView& G, const Unit& U, unsigned* region,
+                                          unsigned* cnt, int64_t* s_base, uint64_t& hits,
+                                          uint64_t& probes, uint64_t& staged) {
+    const int lane = threadIdx.x & 31;
+    const int64_t rb = off_at(G, U.j), re = off_at(G, U.j + 1);
+    const int dp = (int)(re - rb);
+    const int lo = G.adj[rb], hi = G.adj[re - 1];
+    const int mine = (lane < dp) ? G.adj[rb + lane] : 0;
+    const int mine2 = (lane + 32 < dp) ? G.adj[rb + 32 + lane] : 0;
+    const bool bitmap = (int64_t)hi - lo < 32 * kSmallBitWords;
+    uint64_t uh = 0;
+    if (PV)
+        for (int s = lane; s < kSmallTable / 2; s += 32) cnt[s] = 0;
+    if (bitmap) {
+        const int words = ((hi - lo) >> 5) + 1;
+        for (int s = lane; s < words; s += 32) region[s] = 0;
+        __syncwarp();
+        if (lane < dp) atomicOr(&region[(mine - lo) >> 5], 1u << ((mine - lo) & 31));
+        if (lane + 32 < dp) atomicOr(&region[(mine2 - lo) >> 5], 1u << ((mine2 - lo) & 31));
+        __syncwarp();
+        unsigned short* pre = reinterpret_cast<unsigned short*>(region + kSmallBitWords);
+        if (PV) {
+            // prefix popcounts of the (at most 128) words, 4 per lane
+            int a[4], sum = 0;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int wi = lane * 4 + q;
-                        a[q] = (wi < words) ? __popc(region[wi]) : 0;
-                        sum += a[q];
-                    }
-                    int run = warp_incl_scan_i32(sum) - sum;
+            for (int q = 0; q < 4; ++q) {
+                const int wi = lane * 4 + q;
+                a[q] = (wi < words) ? __popc(region[wi]) : 0;
+                sum += a[q];
+            }
+            int run = warp_incl_scan_i32(sum) - sum;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int wi = lane * 4 + q;
-                        if (wi < words) pre[wi] = (unsigned short)run;
-                        run += a[q];
-                    }
-                }
-                __syncwarp();
-                const BitTab T{region, pre, lo, hi};
-                for (int64_t tb = U.t0; tb < U.t1; tb += 32)
-                    warp_probe_group<PV>(tasks, tb, U.t1, adj, T, cnt, tnew, base_s[w], U.t0,
-                                         nullptr, nullptr, uh, probes);
-                __syncwarp();
-                if (PV) {
-                    if (lane < dp) {
-                        const unsigned h = hit_count(cnt, lane);
-                        if (h) atomicAdd(&tnew[mine], (unsigned long long)h);
-                    }
-                    if (lane + 32 < dp) {
-                        const unsigned h = hit_count(cnt, lane + 32);
-                        if (h) atomicAdd(&tnew[mine2], (unsigned long long)h);
-                    }
-                }
-            } else {
-                int* tab = reinterpret_cast<int*>(region);
-                const unsigned bmask = hash_buckets(dp) - 1u;
-                for (int s = lane; s < kSmallTable; s += 32) tab[s] = kEmpty;
-                __syncwarp();
-                if (lane < dp) hash_insert(tab, bmask, mine);
-                if (lane + 32 < dp) hash_insert(tab, bmask, mine2);
-                __syncwarp();
-                const HashTab T{tab, bmask, lo, hi};
-                for (int64_t tb = U.t0; tb < U.t1; tb += 32)
-                    warp_probe_group<PV>(tasks, tb, U.t1, adj, T, cnt, tnew, base_s[w], U.t0,
-                                         nullptr, nullptr, uh, probes);
-                __syncwarp();
-                if (PV) {
-                    for (int s = lane; s < kSmallTable; s += 32) {
-                        const unsigned h = hit_count(cnt, s);
-                        if (h) atomicAdd(&tnew[tab[s]], (unsigned long long)h);
-                    }
-                }
+            for (int q = 0; q < 4; ++q) {
+                const int wi = lane * 4 + q;
+                if (wi < words) pre[wi] = (unsigned short)run;
+                run += a[q];
             }
-            hits += uh;
-            nunit += 1;
-            ntask += (uint64_t)(U.t1 - U.t0);
-            staged += (uint64_t)dp;
-            if (PV) {
-                uh = warp_sum_u64(uh);
-                if (lane == 0 && uh) atomicAdd(&tnew[U.j], (unsigned long long)uh);
-            }
-            __syncwarp();
         }
+        __syncwarp();
+        const BitTab T{region, pre, lo, hi};
+        for (int64_t tb = U.t0; tb < U.t1; tb += 32)
+            warp_probe_group<PV>(G.tasks, tb, U.t1, G.adj, T, cnt, G.tnew, s_base, U.t0, nullptr,
+                                 nullptr, uh, probes);
+        __syncwarp();
+        if (PV) {
+            if (lane < dp) {
+                const unsigned h = hit_count(cnt, lane);
+                if (h) atomicAdd(&G.tnew[mine], (unsigned long long)h);
+            }
+            if (lane + 32 < dp) {
+                const unsigned h = hit_count(cnt, lane + 32);
+                if (h) atomicAdd(&G.tnew[mine2], (unsigned long long)h);
+            }
+        }
+    } else {
+        int* tab = reinterpret_cast<int*>(region);
+        const unsigned bmask = hash_buckets(dp) - 1u;
+        for (int s = lane; s < kSmallTable; s += 32) tab[s] = kEmpty;
+        __syncwarp();
+        if (lane < dp) hash_insert(tab, bmask, mine);
+        if (lane + 32 < dp) hash_insert(tab, bmask, mine2);
+        __syncwarp();
+        const HashTab T{tab, bmask, lo, hi};
+        for (int64_t tb = U.t0; tb < U.t1; tb += 32)
+            warp_probe_group<PV>(G.tasks, tb, U.t1, G.adj, T, cnt, G.tnew, s_base, U.t0, nullptr,
+                                 nullptr, uh, probes);
+        __syncwarp();
+        if (PV)
+            for (int s = lane; s < kSmallTable; s += 32) {
+                const unsigned h = hit_count(cnt, s);
+                if (h) atomicAdd(&G.tnew[tab[s]], (unsigned long long)h);
+            }
     }
-    hits = warp_sum_u64(hits);
-    if (lane == 0) {
-        if (hits) atomicAdd(&ctr[CTR_TOTAL], (unsigned long long)hits);
-        atomicAdd(&ctr[CTR_UNITS + 0], (unsigned long long)nunit);
-        atomicAdd(&ctr[CTR_TASKS + 0], (unsigned long long)ntask);
-        atomicAdd(&ctr[CTR_PROBES + 0], (unsigned long long)probes);
-        atomicAdd(&ctr[CTR_STAGED + 0], (unsigned long long)staged);
+    staged += (uint64_t)dp;
+    hits += uh;
+    if (PV) {
+        uh = warp_sum_u64(uh);
+        if (lane == 0 && uh) atomicAdd(&G.tnew[U.j], (unsigned long long)uh);
     }
+    __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
-// CTA units: a slice of a larger pivot, its table shared by the CTA; warps
-// take groups of 32 tasks from a shared counter until the unit is done.
+// CTA unit: a slice of a larger pivot with its table shared by the CTA.
+// Phase A: warps take groups of 32 tasks from a shared counter, probe the
+// short tails and queue the long ones; phase B: warps pop one long task at a
+// time, the next task's record loaded (and its tail head prefetched) before
+// the current tail is walked.
 // ---------------------------------------------------------------------------
 template <bool PV, class Tab>
-__device__ __forceinline__ void cta_probe_unit(const Task* __restrict__ tasks, const Unit& U,
-                                               const int32_t* __restrict__ adj, const Tab& T,
-                                               unsigned* cnt, unsigned long long* tnew,
-                                               int* s_ctl, int64_t* s_base, unsigned short* s_long,
-                                               uint64_t& uh, uint64_t& probes) {
+__device__ __forceinline__ void cta_probe_unit(const GraphView& G, const Unit& U, const Tab& T,
+                                               unsigned* cnt, int* s_ctl, int64_t* s_base,
+                                               unsigned short* s_long, uint64_t& uh,
+                                               uint64_t& probes) {
     // s_ctl: [0] next group, [1] deferred long tasks, [2] next long task
     const int lane = threadIdx.x & 31;
-    while (true) {   // phase A: groups of 32 tasks, short tails, defer long ones
+    const Task* __restrict__ tasks = G.tasks;
+    const int32_t* __restrict__ adj = G.adj;
+    while (true) {
         int g = 0;
         if (lane == 0) g = atomicAdd(&s_ctl[0], 1);
         g = __shfl_sync(0xffffffffu, g, 0);
         const int64_t tb = U.t0 + (int64_t)g * 32;
         if (tb >= U.t1) break;
-        warp_probe_group<PV>(tasks, tb, U.t1, adj, T, cnt, tnew, s_base, U.t0, s_long, &s_ctl[1],
+        warp_probe_group<PV>(tasks, tb, U.t1, adj, T, cnt, G.tnew, s_base, U.t0, s_long, &s_ctl[1],
                              uh, probes);
     }
     __syncthreads();
     const int nlong = s_ctl[1];
-    // phase B: one long task per warp at a time; the next task's record is
-    // loaded, and its tail's first lines prefetched, before this one is walked
     int x = 0;
     if (lane == 0) x = atomicAdd(&s_ctl[2], 1);
     x = __shfl_sync(0xffffffffu, x, 0);
     Task cur;
+    cur.len = 0;
     if (x < nlong) cur = tasks[U.t0 + s_long[x]];
     while (x < nlong) {
         int xn = 0;
@@ -505,18 +499,110 @@ __device__ __forceinline__ void cta_probe_unit(const Task* __restrict__ tasks, c
         }
         probes += (uint64_t)cur.len;
         const unsigned ch = warp_walk_tail<PV>(cur.start, cur.len, adj, T, cnt, uh);
-        if (PV && lane == 0 && ch) atomicAdd(&tnew[cur.i], (unsigned long long)ch);
+        if (PV && lane == 0 && ch) atomicAdd(&G.tnew[cur.i], (unsigned long long)ch);
         x = xn;
         cur = nxt;
     }
 }
 
-template <class OffT, bool PV>
+template <bool PV>
+__device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int slice_max,
+                                         unsigned* region, unsigned* cnt, int* s_ctl,
+                                         int64_t* s_base, unsigned short* s_long,
+                                         unsigned* s_wsum, unsigned long long* s_red,
+                                         uint64_t& hits, uint64_t& probes) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t rb = off_at(G, U.j) + (int64_t)U.slice * slice_max;
+    const int64_t re = min64(off_at(G, U.j + 1), rb + slice_max);
+    const int dp = (int)(re - rb);
+    const int lo = G.adj[rb], hi = G.adj[re - 1];
+    const bool bitmap = (int64_t)hi - lo < 32ll * kBitWords;
+    uint64_t uh = 0;
+    if (PV)
+        for (int s = threadIdx.x; s < kRegionWords / 2; s += blockDim.x) cnt[s] = 0;
+    if (bitmap) {
+        const int words = ((hi - lo) >> 5) + 1;
+        for (int s = threadIdx.x; s < words; s += blockDim.x) region[s] = 0;
+        __syncthreads();
+        for (int q = threadIdx.x; q < dp; q += blockDim.x) {
+            const int k = G.adj[rb + q] - lo;
+            atomicOr(&region[k >> 5], 1u << (k & 31));
+        }
+        __syncthreads();
+        unsigned short* pre = reinterpret_cast<unsigned short*>(region + kBitWords);
+        if (PV) {
+            // prefix popcounts over the words: each thread a contiguous run
+            const int per = (words + blockDim.x - 1) / blockDim.x;
+            const int w0 = threadIdx.x * per;
+            int sum = 0;
+            for (int q = 0; q < per; ++q)
+                if (w0 + q < words) sum += __popc(region[w0 + q]);
+            const int inc = warp_incl_scan_i32(sum);
+            if (lane == 31) s_wsum[w] = (unsigned)inc;
+            __syncthreads();
+            int before = 0;
+            for (int q = 0; q < w; ++q) before += (int)s_wsum[q];
+            int run = before + inc - sum;
+            for (int q = 0; q < per; ++q)
+                if (w0 + q < words) {
+                    pre[w0 + q] = (unsigned short)run;
+                    run += __popc(region[w0 + q]);
+                }
+            __syncthreads();
+        }
+        const BitTab T{region, pre, lo, hi};
+        cta_probe_unit<PV>(G, U, T, cnt, s_ctl, s_base, s_long, uh, probes);
+        __syncthreads();
+        if (PV)
+            for (int r = threadIdx.x; r < dp; r += blockDim.x) {
+                const unsigned h = hit_count(cnt, r);
+                if (h) atomicAdd(&G.tnew[G.adj[rb + r]], (unsigned long long)h);
+            }
+    } else {
+        int* tab = reinterpret_cast<int*>(region);
+        const unsigned buckets = hash_buckets(dp);
+        const unsigned bmask = buckets - 1u;
+        for (int s = threadIdx.x; s < 4 * (int)buckets; s += blockDim.x) tab[s] = kEmpty;
+        __syncthreads();
+        for (int q = threadIdx.x; q < dp; q += blockDim.x) hash_insert(tab, bmask, G.adj[rb + q]);
+        __syncthreads();
+        const HashTab T{tab, bmask, lo, hi};
+        cta_probe_unit<PV>(G, U, T, cnt, s_ctl, s_base, s_long, uh, probes);
+        __syncthreads();
+        if (PV)
+            for (int s = threadIdx.x; s < 4 * (int)buckets; s += blockDim.x) {
+                const unsigned h = hit_count(cnt, s);
+                if (h) atomicAdd(&G.tnew[tab[s]], (unsigned long long)h);
+            }
+    }
+    hits += uh;
+    if (PV) {
+        uh = warp_sum_u64(uh);
+        if (lane == 0) s_red[w] = uh;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long tot = 0;
+            for (int q = 0; q < nw; ++q) tot += s_red[q];
+            if (tot) atomicAdd(&G.tnew[U.j], tot);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The count kernel: persistent CTAs first pop CTA units (heaviest first),
+// then each warp pops warp units until both queues are empty.  Units may
+// belong to different graphs (the batched form): each carries its graph's
+// index into the view table, and hits are added to that graph's total.
+//
+// Dynamic shared memory: per-warp bases (nw x 32 int64) | table region
+// (kRegionWords words; warp units use 192-word slices of it) | hit counters
+// (PV: kRegionWords/2 words) | long-task queue (unit_tasks x 16 bit).
+// ---------------------------------------------------------------------------
+template <bool PV>
 __global__ void __launch_bounds__(256, TC_LARGE_MINB)
-    k_count_large(const Unit* __restrict__ units, int64_t nunits, const Task* __restrict__ tasks,
-                  const OffT* __restrict__ off, const int32_t* __restrict__ adj, int slice_max,
-                  unsigned long long* __restrict__ ctr, unsigned long long* __restrict__ tnew) {
-    // dynamic shared memory: per-warp bases | table region | counters (PV) | long-task queue
+    k_count(const GraphView* __restrict__ views, const Unit* __restrict__ large, int64_t nlarge,
+            const Unit* __restrict__ small, int64_t nsmall, int slice_max,
+            unsigned long long* __restrict__ ctr) {
     extern __shared__ __align__(16) unsigned smem[];
     __shared__ long long s_unit;
     __shared__ int s_ctl[4];
@@ -527,7 +613,12 @@ __global__ void __launch_bounds__(256, TC_LARGE_MINB)
     unsigned* region = smem + 64 * nw;
     unsigned* cnt = region + kRegionWords;
     unsigned short* s_long = reinterpret_cast<unsigned short*>(cnt + (PV ? kRegionWords / 2 : 0));
-    uint64_t hits = 0, probes = 0, nunit = 0, ntask = 0, staged = 0;
+    __shared__ unsigned long long s_work[6];   // units, tasks, staged for [warp, CTA] units
+    if (threadIdx.x < 6) s_work[threadIdx.x] = 0;
+    GraphAcc acc;
+    uint64_t probes = 0;
+
+    // CTA units
     while (true) {
         if (threadIdx.x == 0) {
             s_unit = (long long)atomicAdd(&ctr[CTR_LARGE_HEAD], 1ull);
@@ -537,98 +628,54 @@ __global__ void __launch_bounds__(256, TC_LARGE_MINB)
         }
         __syncthreads();
         const long long u = s_unit;
-        if (u >= nunits) break;
-        const Unit U = units[u];
-        const int64_t rb = (int64_t)off[U.j] + (int64_t)U.slice * slice_max;
-        const int64_t re = min64((int64_t)off[U.j + 1], rb + slice_max);
-        const int dp = (int)(re - rb);
-        const int lo = adj[rb], hi = adj[re - 1];
-        const bool bitmap = (int64_t)hi - lo < 32ll * kBitWords;
-        uint64_t uh = 0;
-        if (PV)
-            for (int s = threadIdx.x; s < kRegionWords / 2; s += blockDim.x) cnt[s] = 0;
-        if (bitmap) {
-            const int words = ((hi - lo) >> 5) + 1;
-            for (int s = threadIdx.x; s < words; s += blockDim.x) region[s] = 0;
-            __syncthreads();
-            for (int q = threadIdx.x; q < dp; q += blockDim.x) {
-                const int k = adj[rb + q] - lo;
-                atomicOr(&region[k >> 5], 1u << (k & 31));
-            }
-            __syncthreads();
-            unsigned short* pre = reinterpret_cast<unsigned short*>(region + kBitWords);
-            if (PV) {
-                // prefix popcounts over the words: each thread a contiguous run
-                const int per = (words + blockDim.x - 1) / blockDim.x;
-                const int w0 = threadIdx.x * per;
-                int sum = 0;
-                for (int q = 0; q < per; ++q)
-                    if (w0 + q < words) sum += __popc(region[w0 + q]);
-                int inc = warp_incl_scan_i32(sum);
-                if (lane == 31) s_wsum[w] = (unsigned)inc;
-                __syncthreads();
-                int before = 0;
-                for (int q = 0; q < w; ++q) before += (int)s_wsum[q];
-                int run = before + inc - sum;
-                for (int q = 0; q < per; ++q)
-                    if (w0 + q < words) {
-                        pre[w0 + q] = (unsigned short)run;
-                        run += __popc(region[w0 + q]);
-                    }
-                __syncthreads();
-            }
-            const BitTab T{region, pre, lo, hi};
-            cta_probe_unit<PV>(tasks, U, adj, T, cnt, tnew, s_ctl, s_base, s_long, uh, probes);
-            __syncthreads();
-            if (PV)
-                for (int r = threadIdx.x; r < dp; r += blockDim.x) {
-                    const unsigned h = hit_count(cnt, r);
-                    if (h) atomicAdd(&tnew[adj[rb + r]], (unsigned long long)h);
-                }
-        } else {
-            int* tab = reinterpret_cast<int*>(region);
-            const unsigned buckets = hash_buckets(dp);
-            const unsigned bmask = buckets - 1u;
-            for (int s = threadIdx.x; s < 4 * (int)buckets; s += blockDim.x) tab[s] = kEmpty;
-            __syncthreads();
-            for (int q = threadIdx.x; q < dp; q += blockDim.x) hash_insert(tab, bmask, adj[rb + q]);
-            __syncthreads();
-            const HashTab T{tab, bmask, lo, hi};
-            cta_probe_unit<PV>(tasks, U, adj, T, cnt, tnew, s_ctl, s_base, s_long, uh, probes);
-            __syncthreads();
-            if (PV)
-                for (int s = threadIdx.x; s < 4 * (int)buckets; s += blockDim.x) {
-                    const unsigned h = hit_count(cnt, s);
-                    if (h) atomicAdd(&tnew[tab[s]], (unsigned long long)h);
-                }
-        }
-        hits += uh;
+        if (u >= nlarge) break;
+        const Unit U = large[u];
+        acc.to(U.g, views);
+        const GraphView G = views[U.g];
+        cta_unit<PV>(G, U, slice_max, region, cnt, s_ctl, s_base, s_long, s_wsum, s_red, acc.hits,
+                     probes);
         if (threadIdx.x == 0) {
-            nunit += 1;
-            ntask += (uint64_t)(U.t1 - U.t0);
-            staged += (uint64_t)dp;
-        }
-        if (PV) {
-            uh = warp_sum_u64(uh);
-            if (lane == 0) s_red[w] = uh;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                unsigned long long tot = 0;
-                for (int q = 0; q < nw; ++q) tot += s_red[q];
-                if (tot) atomicAdd(&tnew[U.j], tot);
-            }
+            s_work[1] += 1;
+            s_work[3] += (unsigned long long)(U.t1 - U.t0);
+            s_work[5] += (unsigned long long)min64(
+                off_at(G, U.j + 1) - off_at(G, U.j) - (int64_t)U.slice * slice_max, slice_max);
         }
         __syncthreads();
     }
-    hits = warp_sum_u64(hits);
-    if (lane == 0) {
-        if (hits) atomicAdd(&ctr[CTR_TOTAL], (unsigned long long)hits);
-        atomicAdd(&ctr[CTR_PROBES + 1], (unsigned long long)probes);
+    if (lane == 0 && probes) atomicAdd(&ctr[CTR_PROBES + 1], (unsigned long long)probes);
+    probes = 0;
+
+    // warp units, each warp on its own slice of the region
+    unsigned* wregion = region + w * kSmallRegionWords;
+    unsigned* wcnt = cnt + w * (kSmallTable / 2);
+    uint64_t staged = 0;
+    while (true) {
+        long long u0 = 0;
+        if (lane == 0) u0 = (long long)atomicAdd(&ctr[CTR_SMALL_HEAD], (unsigned long long)kGrab);
+        u0 = __shfl_sync(0xffffffffu, u0, 0);
+        if (u0 >= nsmall) break;
+        const int64_t u1 = min64(u0 + kGrab, nsmall);
+        for (int64_t u = u0; u < u1; ++u) {
+            const Unit U = small[u];
+            acc.to(U.g, views);
+            warp_unit<PV>(views[U.g], U, wregion, wcnt, s_base, acc.hits, probes, staged);
+            if (lane == 0) {
+                atomicAdd(&s_work[0], 1ull);
+                atomicAdd(&s_work[2], (unsigned long long)(U.t1 - U.t0));
+            }
+        }
     }
-    if (threadIdx.x == 0) {
-        atomicAdd(&ctr[CTR_UNITS + 1], (unsigned long long)nunit);
-        atomicAdd(&ctr[CTR_TASKS + 1], (unsigned long long)ntask);
-        atomicAdd(&ctr[CTR_STAGED + 1], (unsigned long long)staged);
+    acc.flush(views);
+    if (lane == 0) {
+        if (probes) atomicAdd(&ctr[CTR_PROBES + 0], (unsigned long long)probes);
+        if (staged) atomicAdd(&s_work[4], (unsigned long long)staged);
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        const int k = threadIdx.x;
+        atomicAdd(&ctr[CTR_UNITS + k], s_work[k]);
+        atomicAdd(&ctr[CTR_TASKS + k], s_work[2 + k]);
+        atomicAdd(&ctr[CTR_STAGED + k], s_work[4 + k]);
     }
 }
 
@@ -645,17 +692,31 @@ __global__ void k_copy_total(const unsigned long long* __restrict__ ctr, uint64_
 }
 
 // ---------------------------------------------------------------------------
-// work units
+// Work units over one or many graphs.  Vertex v of the concatenation of the
+// graphs (vpre = prefix of vertex counts) is visited in reverse order, so
+// the last graph's heaviest pivots come first (batches list their graphs by
+// ascending size, so the largest graph leads).
 // ---------------------------------------------------------------------------
-template <class OffT>
-__global__ void k_unit_counts(const OffT* __restrict__ off, const int64_t* __restrict__ loff,
-                              int64_t n, int small_max, int tw, int tcta, int slice,
+__device__ __forceinline__ int find_graph(const int64_t* __restrict__ vpre, int num, int64_t v) {
+    int lo = 0, hi = num - 1;   // largest g with vpre[g] <= v
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (vpre[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_unit_counts(const GraphView* __restrict__ views, const int64_t* __restrict__ vpre,
+                              int num, int64_t V, int small_max, int tw, int tcta, int slice,
                               int32_t* __restrict__ cs, int32_t* __restrict__ cl) {
-    for (int64_t jj = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; jj < n;
-         jj += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = n - 1 - jj;   // heavy pivots (high labels) first
-        const int64_t dp = (int64_t)off[j + 1] - (int64_t)off[j];
-        const int64_t nt = loff[j + 1] - loff[j];
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < V;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = V - 1 - x;
+        const int g = find_graph(vpre, num, v);
+        const GraphView& G = views[g];
+        const int64_t j = v - vpre[g];
+        const int64_t dp = off_at(G, j + 1) - off_at(G, j);
+        const int64_t nt = G.loff[j + 1] - G.loff[j];
         int32_t a = 0, b = 0;
         if (dp > 0 && nt > 0) {
             if (dp <= small_max) {
@@ -665,151 +726,170 @@ __global__ void k_unit_counts(const OffT* __restrict__ off, const int64_t* __res
                 b = (int32_t)(slices * ((nt + tcta - 1) / tcta));
             }
         }
-        cs[jj] = a;
-        cl[jj] = b;
+        cs[x] = a;
+        cl[x] = b;
     }
 }
 
-template <class OffT>
-__global__ void k_unit_fill(const OffT* __restrict__ off, const int64_t* __restrict__ loff,
-                            int64_t n, int small_max, int tw, int tcta, int slice,
+__global__ void k_unit_fill(const GraphView* __restrict__ views, const int64_t* __restrict__ vpre,
+                            int num, int64_t V, int small_max, int tw, int tcta, int slice,
                             const int64_t* __restrict__ ps, const int64_t* __restrict__ pl,
                             Unit* __restrict__ us, Unit* __restrict__ ul) {
-    for (int64_t jj = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; jj < n;
-         jj += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = n - 1 - jj;
-        const int64_t dp = (int64_t)off[j + 1] - (int64_t)off[j];
-        const int64_t a = loff[j], b = loff[j + 1];
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < V;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = V - 1 - x;
+        const int g = find_graph(vpre, num, v);
+        const GraphView& G = views[g];
+        const int64_t j = v - vpre[g];
+        const int64_t dp = off_at(G, j + 1) - off_at(G, j);
+        const int64_t a = G.loff[j], b = G.loff[j + 1];
         if (dp <= 0 || b <= a) continue;
         if (dp <= small_max) {
-            int64_t p = ps[jj];
-            for (int64_t t = a; t < b; t += tw) us[p++] = Unit{(int32_t)j, 0, t, min64(t + tw, b)};
+            int64_t p = ps[x];
+            for (int64_t t = a; t < b; t += tw)
+                us[p++] = Unit{(int32_t)j, 0, g, 0, t, min64(t + tw, b)};
         } else {
             const int64_t slices = (dp + slice - 1) / slice;
-            int64_t p = pl[jj];
+            int64_t p = pl[x];
             for (int64_t t = a; t < b; t += tcta)
                 for (int64_t s = 0; s < slices; ++s)
-                    ul[p++] = Unit{(int32_t)j, (int32_t)s, t, min64(t + tcta, b)};
+                    ul[p++] = Unit{(int32_t)j, (int32_t)s, g, 0, t, min64(t + tcta, b)};
         }
-    }
-}
-
-template <class OffT>
-void build_units_t(tc_graph* g, const tc_tuning& t, cudaStream_t st) {
-    Alloc& al = g->alloc;
-    const int64_t n = g->n;
-    const OffT* off = static_cast<const OffT*>(g->off);
-    const unsigned G = (unsigned)(num_sms() * 8);
-    Buf<int32_t> cs(al, (size_t)std::max<int64_t>(n, 1)), cl(al, (size_t)std::max<int64_t>(n, 1));
-    Buf<int64_t> ps(al, (size_t)(n + 1)), pl(al, (size_t)(n + 1));
-    if (n > 0) {
-        {
-            Prof prof_("k_unit_counts", st);
-            k_unit_counts<OffT><<<grid_for(n, 256, G), 256, 0, st>>>(
-            off, g->loff, n, t.small_max_outdeg, t.warp_unit_tasks, t.cta_unit_tasks, t.slice_max,
-            cs.get(), cl.get());
-        }
-        TC_LAUNCH_CHECK();
-    }
-    exclusive_scan_i32_to_i64(cs.get(), ps.get(), n, ps.get() + n, al, st);
-    exclusive_scan_i32_to_i64(cl.get(), pl.get(), n, pl.get() + n, al, st);
-    int64_t ns = 0, nl = 0;
-    TC_CUDA(cudaMemcpyAsync(&ns, ps.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    TC_CUDA(cudaMemcpyAsync(&nl, pl.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    TC_CUDA(cudaStreamSynchronize(st));
-    if (g->units_mem) {
-        al.put(g->units_mem, g->units_bytes);
-        g->units_mem = nullptr;
-    }
-    g->units_bytes = sizeof(Unit) * (size_t)std::max<int64_t>(ns + nl, 1);
-    g->units_mem = al.get(g->units_bytes);
-    g->small_units = static_cast<Unit*>(g->units_mem);
-    g->large_units = g->small_units + ns;
-    if (n > 0) {
-        {
-            Prof prof_("k_unit_fill", st);
-            k_unit_fill<OffT><<<grid_for(n, 256, G), 256, 0, st>>>(
-            off, g->loff, n, t.small_max_outdeg, t.warp_unit_tasks, t.cta_unit_tasks, t.slice_max,
-            ps.get(), pl.get(), g->small_units, g->large_units);
-        }
-        TC_LAUNCH_CHECK();
-    }
-    g->n_small = ns;
-    g->n_large = nl;
-    g->units_tuning = t;
-    g->stats.small_units = ns;
-    g->stats.large_units = nl;
-}
-
-template <class OffT, bool PV>
-void count_t(const tc_graph* g, const tc_tuning& t, cudaStream_t st) {
-    const OffT* off = static_cast<const OffT*>(g->off);
-    unsigned long long* tnew = reinterpret_cast<unsigned long long*>(g->tnew);
-    const int sms = num_sms();
-    if (g->n_small > 0) {
-        int per_sm = 0;
-        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_small<OffT, PV>,
-                                                              kSmallThreads, 0));
-        per_sm = std::max(per_sm, 1);
-        int64_t need = (g->n_small + kGrab * kSmallWarps - 1) / (kGrab * kSmallWarps);
-        unsigned grid = (unsigned)std::max<int64_t>(1, min64((int64_t)sms * per_sm, need));
-        {
-            Prof prof_("k_count_small", st);
-            k_count_small<OffT, PV><<<grid, kSmallThreads, 0, st>>>(g->small_units, g->n_small, g->tasks,
-                                                               off, g->adj, g->counters, tnew);
-        }
-        TC_LAUNCH_CHECK();
-    }
-    if (g->n_large > 0) {
-        const int threads = t.cta_threads;
-        const size_t smem = sizeof(int64_t) * 32 * (size_t)(threads / 32)
-                            + sizeof(unsigned) * (size_t)(kRegionWords + (PV ? kRegionWords / 2 : 0))
-                            + sizeof(unsigned short) * (size_t)t.cta_unit_tasks;
-        auto kern = k_count_large<OffT, PV>;
-        TC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int per_sm = 0;
-        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
-        per_sm = std::max(per_sm, 1);
-        unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, g->n_large));
-        {
-            Prof prof_("k_count_large", st);
-            kern<<<grid, threads, smem, st>>>(g->large_units, g->n_large, g->tasks, off, g->adj,
-                                              t.slice_max, g->counters, tnew);
-        }
-        TC_LAUNCH_CHECK();
     }
 }
 
 }  // namespace
 
-void build_units(tc_graph* g, const tc_tuning& t, cudaStream_t st) {
+tc_tuning clamp_tuning(const tc_tuning& t) {
     tc_tuning tt = t;
-    tt.slice_max = std::min(tt.slice_max, kRegionWords / 2);
-    if (g->off64)
-        build_units_t<int64_t>(g, tt, st);
-    else
-        build_units_t<int32_t>(g, tt, st);
+    tt.slice_max = std::min(tt.slice_max, kRegionWords / 2);   // a hashed slice needs 2 slots per entry
+    return tt;
+}
+
+UnitLists build_unit_lists(const GraphView* views_dev, const int64_t* vpre_dev, int num, int64_t V,
+                           const tc_tuning& t, Alloc& al, cudaStream_t st) {
+    const unsigned G = (unsigned)(num_sms() * 8);
+    Buf<int32_t> cs(al, (size_t)std::max<int64_t>(V, 1)), cl(al, (size_t)std::max<int64_t>(V, 1));
+    Buf<int64_t> ps(al, (size_t)(V + 1)), pl(al, (size_t)(V + 1));
+    if (V > 0) {
+        Prof prof_("k_unit_counts", st);
+        k_unit_counts<<<grid_for(V, 256, G), 256, 0, st>>>(views_dev, vpre_dev, num, V,
+                                                           t.small_max_outdeg, t.warp_unit_tasks,
+                                                           t.cta_unit_tasks, t.slice_max, cs.get(),
+                                                           cl.get());
+    }
+    TC_LAUNCH_CHECK();
+    exclusive_scan_i32_to_i64(cs.get(), ps.get(), V, ps.get() + V, al, st);
+    exclusive_scan_i32_to_i64(cl.get(), pl.get(), V, pl.get() + V, al, st);
+    int64_t ns = 0, nl = 0;
+    TC_CUDA(cudaMemcpyAsync(&ns, ps.get() + V, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaMemcpyAsync(&nl, pl.get() + V, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    UnitLists L;
+    L.bytes = sizeof(Unit) * (size_t)std::max<int64_t>(ns + nl, 1);
+    L.mem = al.get(L.bytes);
+    L.large = static_cast<Unit*>(L.mem);
+    L.small = L.large + nl;
+    L.nlarge = nl;
+    L.nsmall = ns;
+    if (V > 0) {
+        {
+            Prof prof_("k_unit_fill", st);
+            k_unit_fill<<<grid_for(V, 256, G), 256, 0, st>>>(views_dev, vpre_dev, num, V,
+                                                             t.small_max_outdeg, t.warp_unit_tasks,
+                                                             t.cta_unit_tasks, t.slice_max, ps.get(),
+                                                             pl.get(), L.small, L.large);
+        }
+        TC_LAUNCH_CHECK();
+    }
+    return L;
+}
+
+size_t count_smem_bytes(bool pv, int threads, int unit_tasks) {
+    return sizeof(int64_t) * 32 * (size_t)(threads / 32) +
+           sizeof(unsigned) * (size_t)(kRegionWords + (pv ? kRegionWords / 2 : 0)) +
+           sizeof(unsigned short) * (size_t)unit_tasks;
+}
+
+CountLaunch prepare_count(const UnitLists& L, const tc_tuning& t, bool pv) {
+    CountLaunch c;
+    c.threads = t.cta_threads;
+    c.smem = count_smem_bytes(pv, c.threads, t.cta_unit_tasks);
+    c.pv = pv;
+    auto kern = pv ? k_count<true> : k_count<false>;
+    TC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem));
+    int per_sm = 0;
+    TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, c.threads, c.smem));
+    per_sm = std::max(per_sm, 1);
+    const int64_t want =
+        L.nlarge + (L.nsmall + kGrab * (c.threads / 32) - 1) / (kGrab * (c.threads / 32));
+    c.grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms() * per_sm, want));
+    return c;
+}
+
+void launch_count_raw(const CountLaunch& c, const GraphView* views_dev, const UnitLists& L,
+                      const tc_tuning& t, unsigned long long* ctr, cudaStream_t st) {
+    if (L.nlarge + L.nsmall == 0) return;
+    auto kern = c.pv ? k_count<true> : k_count<false>;
+    kern<<<c.grid, c.threads, c.smem, st>>>(views_dev, L.large, L.nlarge, L.small, L.nsmall,
+                                            t.slice_max, ctr);
+    TC_LAUNCH_CHECK();
+}
+
+void launch_count(const GraphView* views_dev, const UnitLists& L, const tc_tuning& t, bool pv,
+                  unsigned long long* ctr, cudaStream_t st, bool profile) {
+    if (L.nlarge + L.nsmall == 0) return;
+    const CountLaunch c = prepare_count(L, t, pv);
+    if (profile) {
+        Prof prof_("k_count", st);
+        launch_count_raw(c, views_dev, L, t, ctr, st);
+    } else {
+        launch_count_raw(c, views_dev, L, t, ctr, st);
+    }
+}
+
+void build_units(tc_graph* g, const tc_tuning& t, cudaStream_t st) {
+    const tc_tuning tt = clamp_tuning(t);
+    Alloc& al = g->alloc;
+    Buf<int64_t> vpre(al, 2);
+    const int64_t hv[2] = {0, g->n};
+    TC_CUDA(cudaMemcpyAsync(vpre.get(), hv, sizeof(hv), cudaMemcpyHostToDevice, st));
+    UnitLists L = build_unit_lists(g->view, vpre.get(), 1, g->n, tt, al, st);
+    TC_CUDA(cudaStreamSynchronize(st));   // hv lives on this stack frame
+    if (g->units_mem) {
+        al.put(g->units_mem, g->units_bytes);
+        g->units_mem = nullptr;
+    }
+    g->units_mem = L.mem;
+    g->units_bytes = L.bytes;
+    g->small_units = L.small;
+    g->large_units = L.large;
+    g->n_small = L.nsmall;
+    g->n_large = L.nlarge;
+    g->units_tuning = tt;
+    g->stats.small_units = L.nsmall;
+    g->stats.large_units = L.nlarge;
 }
 
 void count(const tc_graph* gc, const tc_tuning& t, uint64_t* total_dev, uint64_t* per_vertex_dev,
            cudaStream_t st) {
     tc_graph* g = const_cast<tc_graph*>(gc);   // unit lists are a cache of the tuning
-    tc_tuning tt = t;
-    tt.slice_max = std::min(tt.slice_max, kRegionWords / 2);   // a hashed slice needs 2 slots per entry
+    const tc_tuning tt = clamp_tuning(t);
     if (!tuning_equal(tt, g->units_tuning)) build_units(g, tt, st);
     const bool pv = per_vertex_dev != nullptr;
     TC_CUDA(cudaMemsetAsync(g->counters, 0, sizeof(unsigned long long) * CTR_COUNT, st));
     if (pv && g->n > 0) TC_CUDA(cudaMemsetAsync(g->tnew, 0, sizeof(uint64_t) * (size_t)g->n, st));
-    if (g->off64) {
-        if (pv) count_t<int64_t, true>(g, tt, st); else count_t<int64_t, false>(g, tt, st);
-    } else {
-        if (pv) count_t<int32_t, true>(g, tt, st); else count_t<int32_t, false>(g, tt, st);
-    }
+    UnitLists L;
+    L.large = g->large_units;
+    L.small = g->small_units;
+    L.nlarge = g->n_large;
+    L.nsmall = g->n_small;
+    launch_count(g->view, L, tt, pv, g->counters, st, true);
     if (pv && g->n > 0) {
         {
             Prof prof_("k_gather_pv", st);
             k_gather_pv<<<grid_for(g->n, 256, num_sms() * 8), 256, 0, st>>>(
-            reinterpret_cast<const unsigned long long*>(g->tnew), g->perm, g->n, per_vertex_dev);
+                reinterpret_cast<const unsigned long long*>(g->tnew), g->perm, g->n, per_vertex_dev);
         }
         TC_LAUNCH_CHECK();
     }

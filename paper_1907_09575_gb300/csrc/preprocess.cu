@@ -273,7 +273,7 @@ void preprocess(tc_graph* g, const int32_t* src_in, const int32_t* dst_in, int64
     size_t sz_perm = align_up(4 * (size_t)std::max<int64_t>(n, 1));
     size_t sz_loff = align_up(8 * (size_t)(n + 1));
     size_t sz_tasks = align_up(sizeof(Task) * (size_t)std::max<int64_t>(m, 1));
-    size_t sz_ctr = align_up(sizeof(unsigned long long) * CTR_COUNT);
+    size_t sz_ctr = align_up(sizeof(unsigned long long) * CTR_COUNT) + align_up(sizeof(GraphView));
     size_t sz_tnew = align_up(8 * (size_t)std::max<int64_t>(n, 1));
     g->arena_bytes = sz_off + sz_adj + sz_perm + sz_loff + sz_tasks + sz_ctr + sz_tnew;
     g->arena = al.get(g->arena_bytes);
@@ -283,7 +283,9 @@ void preprocess(tc_graph* g, const int32_t* src_in, const int32_t* dst_in, int64
     g->perm = reinterpret_cast<int32_t*>(a); a += sz_perm;
     g->loff = reinterpret_cast<int64_t*>(a); a += sz_loff;
     g->tasks = reinterpret_cast<Task*>(a); a += sz_tasks;
-    g->counters = reinterpret_cast<unsigned long long*>(a); a += sz_ctr;
+    g->counters = reinterpret_cast<unsigned long long*>(a);
+    g->view = reinterpret_cast<GraphView*>(a + align_up(sizeof(unsigned long long) * CTR_COUNT));
+    a += sz_ctr;
     g->tnew = reinterpret_cast<uint64_t*>(a);
 
     // a3 max degree, a4 relabel
@@ -409,6 +411,21 @@ void preprocess(tc_graph* g, const int32_t* src_in, const int32_t* dst_in, int64
     g->stats.tasks = ntasks;
     g->stats.probes = hprobes;
     g->stats.offset_bytes = (int32_t)ob;
+
+    // the device view the count kernel reads
+    {
+        GraphView v{};
+        v.off = g->off;
+        v.adj = g->adj;
+        v.loff = g->loff;
+        v.tasks = g->tasks;
+        v.tnew = reinterpret_cast<unsigned long long*>(g->tnew);
+        v.total = g->counters + CTR_TOTAL;
+        v.n = n;
+        v.off64 = g->off64 ? 1 : 0;
+        TC_CUDA(cudaMemcpyAsync(g->view, &v, sizeof(v), cudaMemcpyHostToDevice, st));
+        TC_CUDA(cudaStreamSynchronize(st));
+    }
 
     // work units for the default tuning
     tc_tuning def;

@@ -15,6 +15,33 @@ bool tuning_equal(const tc_tuning& a, const tc_tuning& b);
 
 void preprocess(tc_graph* g, const int32_t* src, const int32_t* dst, int64_t P, uint32_t flags,
                 cudaStream_t st);
+// Unit lists over the graphs of a view table (one graph, or a batch).
+struct UnitLists {
+    void* mem = nullptr;
+    size_t bytes = 0;
+    Unit* large = nullptr;
+    Unit* small = nullptr;
+    int64_t nlarge = 0, nsmall = 0;
+};
+
+tc_tuning clamp_tuning(const tc_tuning& t);
+UnitLists build_unit_lists(const GraphView* views_dev, const int64_t* vpre_dev, int num, int64_t V,
+                           const tc_tuning& t, Alloc& al, cudaStream_t st);
+size_t count_smem_bytes(bool pv, int threads, int unit_tasks);
+struct CountLaunch {
+    unsigned grid = 1;
+    int threads = 256;
+    size_t smem = 0;
+    bool pv = false;
+};
+// Sets the kernel's shared-memory attribute and sizes the persistent grid
+// (not a stream operation: call it outside stream capture).
+CountLaunch prepare_count(const UnitLists& L, const tc_tuning& t, bool pv);
+void launch_count_raw(const CountLaunch& c, const GraphView* views_dev, const UnitLists& L,
+                      const tc_tuning& t, unsigned long long* ctr, cudaStream_t st);
+// Launches the count kernel; ctr holds the queue heads and work counters.
+void launch_count(const GraphView* views_dev, const UnitLists& L, const tc_tuning& t, bool pv,
+                  unsigned long long* ctr, cudaStream_t st, bool profile);
 void build_units(tc_graph* g, const tc_tuning& t, cudaStream_t st);
 void count(const tc_graph* g, const tc_tuning& t, uint64_t* total_dev, uint64_t* per_vertex_dev,
            cudaStream_t st);

@@ -63,7 +63,9 @@ _lib: Optional[ctypes.CDLL] = None
 # Every symbol include/tc.h declares (checked by the tests).
 EXPORTS = ("tc_preprocess", "tc_count", "tc_triangles", "tc_graph_get_stats", "tc_graph_free",
            "tc_tuning_default", "tc_last_error", "tc_generate_rmat", "tc_kernel_launches",
-           "tc_profile_enable", "tc_profile_read", "tc_count_get_stats", "tc_triangles_static")
+           "tc_profile_enable", "tc_profile_read", "tc_count_get_stats", "tc_triangles_static",
+           "tc_batch_create", "tc_batch_count", "tc_batch_autotune", "tc_batch_get_count_stats",
+           "tc_batch_free", "tc_count_batch")
 
 TC_STATIC_MAX_PAIRS = 262144
 TC_STATIC_MAX_VERTICES = 65536
@@ -109,6 +111,18 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tc_generate_rmat.restype = st
     lib.tc_count_get_stats.argtypes = [vp, ctypes.POINTER(CountStats), vp]
     lib.tc_count_get_stats.restype = st
+    lib.tc_batch_create.argtypes = [vp, i32, vp, vp, ctypes.POINTER(vp)]
+    lib.tc_batch_create.restype = st
+    lib.tc_batch_count.argtypes = [vp, vp, vp]
+    lib.tc_batch_count.restype = st
+    lib.tc_batch_autotune.argtypes = [vp, i32, ctypes.POINTER(Tuning), vp]
+    lib.tc_batch_autotune.restype = st
+    lib.tc_batch_get_count_stats.argtypes = [vp, ctypes.POINTER(CountStats), vp]
+    lib.tc_batch_get_count_stats.restype = st
+    lib.tc_batch_free.argtypes = [vp]
+    lib.tc_batch_free.restype = None
+    lib.tc_count_batch.argtypes = [vp, i32, vp, vp, vp]
+    lib.tc_count_batch.restype = st
     lib.tc_triangles_static.argtypes = [vp, vp, i64, i64, vp, vp, vp]
     lib.tc_triangles_static.restype = st
     lib.tc_kernel_launches.argtypes = []
@@ -228,6 +242,62 @@ class Graph:
         if per_vertex is True:
             return t, pv[: self.n]
         return t
+
+
+class Batch:
+    """tc_batch_*: many graphs counted by one persistent launch (replayed
+    from a captured CUDA graph).  The graphs must outlive the batch."""
+
+    def __init__(self, graphs, tuning: Optional[Tuning] = None):
+        self.graphs = list(graphs)
+        arr = (ctypes.c_void_p * len(self.graphs))(*[g.handle for g in self.graphs])
+        h = ctypes.c_void_p(0)
+        _check(load().tc_batch_create(arr, len(self.graphs),
+                                      ctypes.byref(tuning) if tuning is not None else None,
+                                      None, ctypes.byref(h)))
+        self._h = h
+
+    def count(self, totals=None, stream=None):
+        """Counts every graph; returns (and fills) a CUDA int64 tensor of totals."""
+        import torch
+        if totals is None:
+            totals = torch.empty(len(self.graphs), dtype=torch.int64, device="cuda")
+        _check(load().tc_batch_count(self._h, totals.data_ptr(), _stream_ptr(stream)))
+        return totals
+
+    def autotune(self, reps: int = 3, stream=None) -> Tuning:
+        t = Tuning()
+        _check(load().tc_batch_autotune(self._h, reps, ctypes.byref(t), _stream_ptr(stream)))
+        return t
+
+    def count_stats(self, stream=None) -> dict:
+        c = CountStats()
+        _check(load().tc_batch_get_count_stats(self._h, ctypes.byref(c), _stream_ptr(stream)))
+        return {"triangles": int(c.triangles), "units": list(c.units), "tasks": list(c.tasks),
+                "probes": list(c.probes), "staged": list(c.staged)}
+
+    def free(self) -> None:
+        if self._h.value:
+            load().tc_batch_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def count_batch(graphs, tuning: Optional[Tuning] = None, stream=None):
+    """tc_count_batch: one-shot batched count; returns a CUDA int64 tensor."""
+    import torch
+    graphs = list(graphs)
+    arr = (ctypes.c_void_p * len(graphs))(*[g.handle for g in graphs])
+    totals = torch.empty(len(graphs), dtype=torch.int64, device="cuda")
+    _check(load().tc_count_batch(arr, len(graphs),
+                                 ctypes.byref(tuning) if tuning is not None else None,
+                                 totals.data_ptr(), _stream_ptr(stream)))
+    return totals
 
 
 def preprocess(src, dst, n: int, offsets: Optional[int] = None, stream=None,

@@ -1,0 +1,99 @@
+"""Batched counting (one persistent launch over many graphs) against the
+oracle and against counting each graph alone.  Counts are integers: exact."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1907_09575_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tc():
+    from paper_1907_09575_gb300 import tc as _tc
+    _tc.load()
+    return _tc
+
+
+def small_batch(seed, count, max_log_n=12):
+    """Uneven graphs shaped like the 4096-graph batch, scaled down."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for g in range(count):
+        n = int(2 ** rng.uniform(4, max_log_n))
+        d = float(rng.uniform(2, 40))
+        if g % 2 == 0:
+            specs.append(inputs.GraphSpec("gnp", seed * 1000 + g, max(n, 2), p=min(1.0, d / max(n - 1, 1))))
+        else:
+            scale = max(1, int(np.ceil(np.log2(max(n, 2)))))
+            specs.append(inputs.GraphSpec("rmat", seed * 1000 + g, max(n, 2),
+                                          num_pairs=int(n * d / 2), scale=scale))
+    return specs
+
+
+def build(tc, specs, offsets=None):
+    graphs, want = [], []
+    for k, sp in enumerate(specs):
+        s, d = sp.generate()
+        want.append(oracle.count(s, d, sp.n))
+        off = offsets if offsets is not None else (32 if k % 3 else 64)
+        graphs.append(tc.preprocess(s, d, sp.n, offsets=off))
+    return graphs, want
+
+
+def test_batch_matches_oracle_and_single_counts(tc):
+    specs = small_batch(1, 96)
+    graphs, want = build(tc, specs)
+    b = tc.Batch(graphs)
+    got = b.count().cpu().numpy()
+    assert got.tolist() == want
+    # the same graphs counted one per launch
+    assert [g.count() for g in graphs] == want
+    # replaying the captured launch gives the same totals
+    assert b.count().cpu().numpy().tolist() == want
+    st = b.count_stats()
+    assert st["triangles"] == sum(want)
+    b.free()
+    for g in graphs:
+        g.free()
+
+
+def test_batch_edge_cases(tc):
+    specs = [inputs.GraphSpec("gnp", 5, 2, p=0.0),                 # no edges
+             inputs.GraphSpec("gnp", 6, 30, p=1.0),                # K_30: warp and CTA units
+             inputs.rmat_graph(7, 10, 16)]
+    graphs, want = build(tc, specs)
+    e = [(a, b) for a in range(200) for b in range(a + 1, 200)]    # K_200
+    s = np.array([x for x, _ in e], np.int32)
+    d = np.array([y for _, y in e], np.int32)
+    graphs.append(tc.preprocess(s, d, 200))
+    want.append(200 * 199 * 198 // 6)
+    assert tc.count_batch(graphs).cpu().numpy().tolist() == want
+    b = tc.Batch(graphs[1:2])   # a batch of one
+    assert b.count().cpu().numpy().tolist() == want[1:2]
+    b.free()
+    for g in graphs:
+        g.free()
+
+
+def test_batch_autotune_keeps_counts(tc):
+    specs = small_batch(3, 40, max_log_n=13)
+    graphs, want = build(tc, specs, offsets=32)
+    b = tc.Batch(graphs)
+    t = b.autotune(reps=1)
+    assert t.small_max_outdeg in (16, 64) and t.cta_threads in (128, 256)
+    assert b.count().cpu().numpy().tolist() == want
+    # a second batch with the same profile reuses the cached choice
+    b2 = tc.Batch(graphs)
+    t2 = b2.autotune(reps=1)
+    assert (t2.small_max_outdeg, t2.warp_unit_tasks, t2.cta_unit_tasks, t2.cta_threads) == \
+           (t.small_max_outdeg, t.warp_unit_tasks, t.cta_unit_tasks, t.cta_threads)
+    assert b2.count().cpu().numpy().tolist() == want
+    for x in (b, b2):
+        x.free()
+    for g in graphs:
+        g.free()
