@@ -147,6 +147,36 @@ TC_API tc_status tc_count(const tc_graph* g, const tc_tuning* tune, uint64_t* to
                    uint64_t* total_dev, uint64_t* per_vertex_dev, void* stream);
 
 /*
+ * tc_preprocess_components -- tc_preprocess of a disjoint union of graphs
+ * whose vertex ranges are [vertex_prefix[c], vertex_prefix[c+1]) for
+ * components c = 0..num_comps-1.  Any total order of the vertices orients U
+ * correctly (Section 3.1 only asks for degree order to save work), so the
+ * union is relabelled by degree as one graph; every triangle lies inside one
+ * component, and tc_count_components credits each to its component.
+ *
+ *   vertex_prefix  host array of num_comps + 1 int64, vertex_prefix[0] = 0,
+ *                  non-decreasing; n = vertex_prefix[num_comps].
+ *   num_comps      >= 1.
+ *   Other arguments as tc_preprocess.  Every pair must join two vertices of
+ *   one component (checked on the device).
+ * Errors: as tc_preprocess, plus TC_EINVAL for a bad prefix or a pair that
+ * joins two components.  Synchronises the stream.
+ */
+TC_API tc_status tc_preprocess_components(const int32_t* src, const int32_t* dst, int64_t num_pairs,
+                                          const int64_t* vertex_prefix, int32_t num_comps,
+                                          uint32_t flags, const tc_allocator* alloc, void* stream,
+                                          tc_graph** out);
+
+/*
+ * tc_count_components -- Eq. 1 / Eq. 2 per component of a graph from
+ * tc_preprocess_components: comp_totals_dev (device, num_comps uint64)
+ * receives each component's triangle count.  Stream ordered.
+ * Errors: TC_EINVAL for NULL arguments or a graph without components.
+ */
+TC_API tc_status tc_count_components(const tc_graph* g, const tc_tuning* tune,
+                                     uint64_t* comp_totals_dev, void* stream);
+
+/*
  * tc_triangles -- one call from host pair lists to host results: H2D copy,
  * tc_preprocess, tc_count, D2H copy, release.  Same arguments and errors as
  * the two calls it makes; total_host must be non-NULL, per_vertex_host is
@@ -231,6 +261,73 @@ TC_API tc_status tc_batch_get_count_stats(const tc_batch* b, tc_count_stats* out
 TC_API void tc_batch_free(tc_batch* b);
 TC_API tc_status tc_count_batch(const tc_graph* const* graphs, int32_t num, const tc_tuning* tune,
                                 uint64_t* totals_dev, void* stream);
+
+/*
+ * Serving (no counterpart in the paper).  A server takes count requests --
+ * seeded RMAT specs, expanded on the device -- in arrival order and runs
+ * them in ticks: worker threads (one CUDA stream each) take requests from
+ * the head of the queue while the tick stays within max_batch requests and
+ * max_tick_pairs pairs and the device bytes of all ticks in flight stay
+ * within hbm_budget_bytes (each request's footprint is estimated as
+ * 64 B per pair + 48 B per vertex); a tick's requests are preprocessed as one
+ * disjoint union and counted per component (tc_preprocess_components /
+ * tc_count_components).  Ticks on different workers overlap on the device.
+ * Results carry the caller-given arrival time and the server-clock times of
+ * admission and completion (tc_server_now: seconds since creation).
+ *
+ * tc_server_create: cfg may be NULL (all defaults); zero or negative size
+ *   fields take defaults (16 GiB budget, 2 workers, 512 requests and 2^27
+ *   pairs per tick); device -1 (or NULL cfg) uses the current device.
+ * tc_server_submit_rmat: queue one request; *ticket (may be NULL) gets its
+ *   id.  TC_EINVAL for a bad spec; TC_EBUSY if the request alone exceeds the
+ *   budget (it is dropped).
+ * tc_server_poll: move up to max finished results to out (waiting up to
+ *   wait_ms for the first); *count gets how many.
+ * tc_server_drain: wait until every submitted request is done; TC_ETIMEOUT
+ *   after timeout_ms (the requests stay queued), else the first error any
+ *   tick met (TC_OK if none).
+ * tc_server_free: finishes the ticks in flight and the queued requests that
+ *   fit, stops the workers, frees the server.
+ */
+typedef struct tc_server tc_server;
+typedef struct {
+    int64_t hbm_budget_bytes;
+    int32_t workers;
+    int32_t max_batch;
+    int64_t max_tick_pairs;
+    int32_t device;        /* CUDA device; -1 for the calling thread's current one */
+    int32_t pad;
+} tc_server_config;
+typedef struct {
+    uint64_t seed;
+    int32_t scale;         /* ids drawn on [0, 2^scale), those >= n redrawn */
+    int32_t pad;
+    int64_t n;             /* vertices, 1 <= n <= 2^scale */
+    int64_t num_pairs;     /* generated pairs */
+    uint32_t t1, t2, t3;   /* cumulative a, a+b, a+b+c scaled to 2^32 */
+    uint32_t pad2;
+} tc_rmat_spec;
+typedef struct {
+    int64_t ticket;
+    uint64_t triangles;
+    double t_arrival, t_admit, t_done;
+    int32_t status;        /* TC_OK, or the error of the request's tick */
+    int32_t tick_requests; /* requests counted in the same tick */
+} tc_server_result;
+typedef struct {
+    int64_t submitted, completed, failed, pending, ticks;
+    int64_t bytes_in_flight, peak_bytes_in_flight, busy_workers;
+} tc_server_stats;
+
+TC_API tc_status tc_server_create(const tc_server_config* cfg, tc_server** out);
+TC_API double tc_server_now(const tc_server* s);
+TC_API tc_status tc_server_submit_rmat(tc_server* s, const tc_rmat_spec* spec, double t_arrival,
+                                       int64_t* ticket);
+TC_API tc_status tc_server_poll(tc_server* s, tc_server_result* out, int32_t max, int32_t* count,
+                                int32_t wait_ms);
+TC_API tc_status tc_server_drain(tc_server* s, int32_t timeout_ms);
+TC_API tc_status tc_server_get_stats(tc_server* s, tc_server_stats* out);
+TC_API void tc_server_free(tc_server* s);
 
 /*
  * tc_triangles_static -- tc_preprocess + tc_count for a small graph with no

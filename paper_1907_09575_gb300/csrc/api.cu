@@ -145,6 +145,61 @@ tc_status tc_preprocess(const int32_t* src, const int32_t* dst, int64_t num_pair
     TC_API_END
 }
 
+tc_status tc_preprocess_components(const int32_t* src, const int32_t* dst, int64_t num_pairs,
+                                   const int64_t* vertex_prefix, int32_t num_comps, uint32_t flags,
+                                   const tc_allocator* alloc, void* stream, tc_graph** out) {
+    TC_API_BEGIN
+    if (!out || !vertex_prefix || num_comps <= 0)
+        TC_FAIL(TC_EINVAL, "tc_preprocess_components: need out, vertex_prefix and num_comps > 0");
+    if (vertex_prefix[0] != 0) TC_FAIL(TC_EINVAL, "tc_preprocess_components: vertex_prefix[0] != 0");
+    for (int32_t c = 0; c < num_comps; ++c)
+        if (vertex_prefix[c + 1] < vertex_prefix[c])
+            TC_FAIL(TC_EINVAL, "tc_preprocess_components: vertex_prefix decreases at %d", c);
+    const int64_t n = vertex_prefix[num_comps];
+    if (num_pairs < 0) TC_FAIL(TC_EINVAL, "tc_preprocess_components: num_pairs < 0");
+    if (n >= (int64_t)0x7fffffff) TC_FAIL(TC_EINVAL, "tc_preprocess_components: n >= 2^31-1");
+    if (num_pairs > 0 && (!src || !dst)) TC_FAIL(TC_EINVAL, "tc_preprocess_components: src or dst is NULL");
+    if (num_pairs > (int64_t)0x7fffffff) TC_FAIL(TC_EINVAL, "tc_preprocess_components: num_pairs >= 2^31");
+    if ((flags & TC_OFFSETS_32) && (flags & TC_OFFSETS_64))
+        TC_FAIL(TC_EINVAL, "tc_preprocess_components: both offset widths requested");
+    if (alloc && (!alloc->alloc || !alloc->free))
+        TC_FAIL(TC_EINVAL, "tc_preprocess_components: allocator without alloc/free");
+    tc_graph* g = new tc_graph();
+    g->n = n;
+    g->num_pairs = num_pairs;
+    g->bits = std::max(1, ceil_log2_u64((uint64_t)std::max<int64_t>(n, 1)));
+    g->alloc.stream = static_cast<cudaStream_t>(stream);
+    if (alloc) {
+        g->alloc.user = *alloc;
+        g->alloc.has_user = true;
+    }
+    g->stats.n = n;
+    g->stats.num_pairs = num_pairs;
+    try {
+        preprocess_with_components(g, src, dst, num_pairs, flags, vertex_prefix, num_comps,
+                                   static_cast<cudaStream_t>(stream));
+    } catch (...) {
+        graph_release(g);
+        throw;
+    }
+    *out = g;
+    TC_API_END
+}
+
+tc_status tc_count_components(const tc_graph* g, const tc_tuning* tune, uint64_t* comp_totals_dev,
+                              void* stream) {
+    TC_API_BEGIN
+    if (!g || !comp_totals_dev) TC_FAIL(TC_EINVAL, "tc_count_components: NULL argument");
+    if (g->num_comps <= 0 || !g->comp)
+        TC_FAIL(TC_EINVAL, "tc_count_components: graph was not preprocessed with components");
+    tc_tuning t;
+    tuning_resolve(tune, &t);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const_cast<tc_graph*>(g)->alloc.stream = st;
+    count_components(g, t, comp_totals_dev, st);
+    TC_API_END
+}
+
 tc_status tc_count(const tc_graph* g, const tc_tuning* tune, uint64_t* total_host,
                    uint64_t* total_dev, uint64_t* per_vertex_dev, void* stream) {
     TC_API_BEGIN

@@ -156,6 +156,10 @@ struct tc_graph {
     struct Unit* large_units = nullptr;
     unsigned long long* counters = nullptr;  // queue heads and totals (device)
     struct GraphView* view = nullptr;        // device copy of this graph's view
+    struct GraphView* view_comp = nullptr;   // same, hits credited per component
+    int32_t* comp = nullptr;                 // component of each new label (or null)
+    unsigned long long* comp_totals = nullptr;
+    int32_t num_comps = 0;
     uint64_t* tnew = nullptr;   // per-vertex accumulator in new labels, n
 
     int64_t n_tasks = 0, n_small = 0, n_large = 0;
@@ -191,6 +195,8 @@ struct GraphView {
     const Task* tasks;
     unsigned long long* tnew;     // per-vertex accumulator (new labels), or null
     unsigned long long* total;    // where this graph's hits are added
+    const int32_t* comp;          // component of each new label, or null
+    unsigned long long* comp_totals;   // per-component totals (with comp)
     int64_t n;
     int32_t off64;
     int32_t pad;

@@ -347,19 +347,25 @@ __device__ __forceinline__ int64_t off_at(const GraphView& G, int64_t v) {
                    : (int64_t) static_cast<const int32_t*>(G.off)[v];
 }
 
-// Per-warp running total of one graph's hits, flushed to that graph's total
-// when the warp moves to a unit of another graph (and at the end).
+// Per-warp running total of hits bound for one counter (a graph's total, or
+// a component's total), flushed when the warp moves to a unit whose hits go
+// elsewhere (and at the end).  Every triangle found at pivot j lies in j's
+// component, so the pivot decides the counter.
+__device__ __forceinline__ unsigned long long* unit_target(const GraphView& G, const Unit& U) {
+    return G.comp ? G.comp_totals + G.comp[U.j] : G.total;
+}
+
 struct GraphAcc {
-    int g = -1;
+    unsigned long long* target = nullptr;
     uint64_t hits = 0;
-    __device__ __forceinline__ void to(int ng, const GraphView* __restrict__ views) {
-        if (ng == g) return;
-        flush(views);
-        g = ng;
+    __device__ __forceinline__ void to(unsigned long long* t) {
+        if (t == target) return;
+        flush();
+        target = t;
     }
-    __device__ __forceinline__ void flush(const GraphView* __restrict__ views) {
+    __device__ __forceinline__ void flush() {
         const uint64_t s = warp_sum_u64(hits);
-        if ((threadIdx.x & 31) == 0 && g >= 0 && s) atomicAdd(views[g].total, (unsigned long long)s);
+        if ((threadIdx.x & 31) == 0 && target && s) atomicAdd(target, (unsigned long long)s);
         hits = 0;
     }
 };
@@ -630,8 +636,8 @@ __global__ void __launch_bounds__(256, TC_LARGE_MINB)
         const long long u = s_unit;
         if (u >= nlarge) break;
         const Unit U = large[u];
-        acc.to(U.g, views);
         const GraphView G = views[U.g];
+        acc.to(unit_target(G, U));
         cta_unit<PV>(G, U, slice_max, region, cnt, s_ctl, s_base, s_long, s_wsum, s_red, acc.hits,
                      probes);
         if (threadIdx.x == 0) {
@@ -657,15 +663,16 @@ __global__ void __launch_bounds__(256, TC_LARGE_MINB)
         const int64_t u1 = min64(u0 + kGrab, nsmall);
         for (int64_t u = u0; u < u1; ++u) {
             const Unit U = small[u];
-            acc.to(U.g, views);
-            warp_unit<PV>(views[U.g], U, wregion, wcnt, s_base, acc.hits, probes, staged);
+            const GraphView G = views[U.g];
+            acc.to(unit_target(G, U));
+            warp_unit<PV>(G, U, wregion, wcnt, s_base, acc.hits, probes, staged);
             if (lane == 0) {
                 atomicAdd(&s_work[0], 1ull);
                 atomicAdd(&s_work[2], (unsigned long long)(U.t1 - U.t0));
             }
         }
     }
-    acc.flush(views);
+    acc.flush();
     if (lane == 0) {
         if (probes) atomicAdd(&ctr[CTR_PROBES + 0], (unsigned long long)probes);
         if (staged) atomicAdd(&s_work[4], (unsigned long long)staged);
@@ -869,6 +876,23 @@ void build_units(tc_graph* g, const tc_tuning& t, cudaStream_t st) {
     g->units_tuning = tt;
     g->stats.small_units = L.nsmall;
     g->stats.large_units = L.nlarge;
+}
+
+void count_components(const tc_graph* gc, const tc_tuning& t, uint64_t* comp_totals_dev,
+                      cudaStream_t st) {
+    tc_graph* g = const_cast<tc_graph*>(gc);
+    const tc_tuning tt = clamp_tuning(t);
+    if (!tuning_equal(tt, g->units_tuning)) build_units(g, tt, st);
+    TC_CUDA(cudaMemsetAsync(g->counters, 0, sizeof(unsigned long long) * CTR_COUNT, st));
+    TC_CUDA(cudaMemsetAsync(g->comp_totals, 0, sizeof(unsigned long long) * (size_t)g->num_comps, st));
+    UnitLists L;
+    L.large = g->large_units;
+    L.small = g->small_units;
+    L.nlarge = g->n_large;
+    L.nsmall = g->n_small;
+    launch_count(g->view_comp, L, tt, false, g->counters, st, true);
+    TC_CUDA(cudaMemcpyAsync(comp_totals_dev, g->comp_totals, sizeof(uint64_t) * (size_t)g->num_comps,
+                            cudaMemcpyDeviceToDevice, st));
 }
 
 void count(const tc_graph* gc, const tc_tuning& t, uint64_t* total_dev, uint64_t* per_vertex_dev,

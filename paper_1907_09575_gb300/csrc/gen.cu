@@ -7,6 +7,7 @@
 // xor B) * C mod 2^s, and rejection of ids >= n (64 attempts, then the
 // self-loop (0,0)).  Equal output for equal (seed, scale, n, pair index).
 #include "common.cuh"
+#include "tc_internal.cuh"
 
 namespace tc {
 namespace {
@@ -59,7 +60,78 @@ __global__ void k_rmat(uint64_t key, int scale, uint64_t n, int64_t e0, int64_t 
     }
 }
 
+// Many RMAT requests at once: pair x of the concatenation belongs to the
+// request r with ppre[r] <= x < ppre[r+1]; its ids are offset by vpre[r].
+__global__ void k_rmat_multi(const RmatJob* __restrict__ jobs, const int64_t* __restrict__ ppre,
+                             int nreq, int64_t total, int32_t* __restrict__ src,
+                             int32_t* __restrict__ dst) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nreq - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (ppre[mid] <= x) lo = mid; else hi = mid - 1;
+        }
+        const RmatJob& J = jobs[lo];
+        const uint64_t e = (uint64_t)(x - ppre[lo]);
+        const uint64_t mask = (1ull << J.scale) - 1ull;
+        const uint64_t hpa = (uint64_t)((J.scale + 1) / 2);
+        int64_t su = 0, sv = 0;
+        for (int a = 0; a < kAttempts; ++a) {
+            const uint64_t base = (e * kAttempts + (uint64_t)a) * hpa;
+            uint64_t u = 0, v = 0, h = 0;
+            for (int l = 0; l < J.scale; ++l) {
+                if ((l & 1) == 0) h = draw(J.key, base + (uint64_t)(l >> 1));
+                const uint32_t r = (l & 1) ? (uint32_t)(h >> 32) : (uint32_t)h;
+                const uint64_t bu = (r >= J.t2) ? 1ull : 0ull;
+                const uint64_t bv = (r >= J.t1 && r < J.t2) || (r >= J.t3) ? 1ull : 0ull;
+                u = (u << 1) | bu;
+                v = (v << 1) | bv;
+            }
+            u = ((((u * J.A) & mask) ^ J.B) * J.C) & mask;
+            v = ((((v * J.A) & mask) ^ J.B) * J.C) & mask;
+            if (u < (uint64_t)J.n && v < (uint64_t)J.n) {
+                su = (int64_t)u;
+                sv = (int64_t)v;
+                break;
+            }
+        }
+        src[x] = (int32_t)(J.vbase + su);
+        dst[x] = (int32_t)(J.vbase + sv);
+    }
+}
+
 }  // namespace
+
+RmatJob make_rmat_job(uint64_t seed, int scale, int64_t n, uint32_t t1, uint32_t t2, uint32_t t3,
+                      int64_t vbase) {
+    RmatJob J;
+    J.key = mix64(seed * kGamma + kTagPairs);
+    const uint64_t ks = mix64(seed * kGamma + kTagScramble);
+    const uint64_t mask = (1ull << scale) - 1ull;
+    J.A = (draw(ks, 0) | 1ull) & mask;
+    J.B = draw(ks, 1) & mask;
+    J.C = (draw(ks, 2) | 1ull) & mask;
+    J.n = n;
+    J.vbase = vbase;
+    J.scale = scale;
+    J.t1 = t1;
+    J.t2 = t2;
+    J.t3 = t3;
+    return J;
+}
+
+void generate_rmat_multi(const RmatJob* jobs_dev, const int64_t* ppre_dev, int nreq, int64_t total,
+                         int32_t* src, int32_t* dst, cudaStream_t st) {
+    if (total <= 0) return;
+    {
+        Prof prof_("k_rmat_multi", st);
+        k_rmat_multi<<<grid_for(total, 256, (int64_t)num_sms() * 16), 256, 0, st>>>(
+            jobs_dev, ppre_dev, nreq, total, src, dst);
+    }
+    TC_LAUNCH_CHECK();
+}
+
 }  // namespace tc
 
 using namespace tc;

@@ -192,10 +192,41 @@ __global__ void k_max_outdeg(const OffT* __restrict__ off, int64_t n, int* __res
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
+// component of vertex v: largest c with vpre[c] <= v
+__device__ __forceinline__ int comp_of(const int64_t* __restrict__ vpre, int num, int64_t v) {
+    int lo = 0, hi = num - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (vpre[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_check_comp(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                             int64_t P, const int64_t* __restrict__ vpre, int num,
+                             int* __restrict__ err) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P;
+         e += (int64_t)gridDim.x * blockDim.x)
+        if (comp_of(vpre, num, src[e]) != comp_of(vpre, num, dst[e])) atomicOr(err, 2);
+}
+
+__global__ void k_comp_new(const int32_t* __restrict__ perm, int64_t n, const int64_t* __restrict__ vpre,
+                           int num, int32_t* __restrict__ comp) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        comp[perm[v]] = comp_of(vpre, num, v);
+}
+
 }  // namespace
 
 void preprocess(tc_graph* g, const int32_t* src_in, const int32_t* dst_in, int64_t P,
                 uint32_t flags, cudaStream_t st) {
+    preprocess_with_components(g, src_in, dst_in, P, flags, nullptr, 0, st);
+}
+
+void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_t* dst_in, int64_t P,
+                                uint32_t flags, const int64_t* vpre_host, int32_t num_comps,
+                                cudaStream_t st) {
     Alloc& al = g->alloc;
     const int64_t n = g->n;
     const int bits = g->bits;
@@ -217,6 +248,13 @@ void preprocess(tc_graph* g, const int32_t* src_in, const int32_t* dst_in, int64
 
     Buf<int> scal(al, 8);   // [0] err, [1] max degree, [2] max out-degree
     TC_CUDA(cudaMemsetAsync(scal.get(), 0, 8 * sizeof(int), st));
+    Buf<int64_t> vpre;
+    if (num_comps > 0) {
+        vpre = Buf<int64_t>(al, (size_t)num_comps + 1);
+        TC_CUDA(cudaMemcpyAsync(vpre.get(), vpre_host, sizeof(int64_t) * (size_t)(num_comps + 1),
+                                cudaMemcpyHostToDevice, st));
+        TC_CUDA(cudaStreamSynchronize(st));   // vpre_host may go away after the call
+    }
     Buf<int64_t> tot(al, 4);  // [0] m, [1] tasks
 
     // a1 + a2: canonical keys, sorted, unique
@@ -233,10 +271,16 @@ void preprocess(tc_graph* g, const int32_t* src_in, const int32_t* dst_in, int64
             k_canon<<<grid_for(P, kT, G), kT, 0, st>>>(src, dst, P, n, bits, sentinel, keys, scal.get());
         }
         TC_LAUNCH_CHECK();
+        if (num_comps > 0) {
+            Prof prof_("k_check_comp", st);
+            k_check_comp<<<grid_for(P, kT, G), kT, 0, st>>>(src, dst, P, vpre.get(), num_comps, scal.get());
+        }
+        TC_LAUNCH_CHECK();
         int err = 0;
         TC_CUDA(cudaMemcpyAsync(&err, scal.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
         TC_CUDA(cudaStreamSynchronize(st));
-        if (err) TC_FAIL(TC_EINVAL, "tc_preprocess: a vertex id lies outside [0, n)");
+        if (err & 1) TC_FAIL(TC_EINVAL, "tc_preprocess: a vertex id lies outside [0, n)");
+        if (err & 2) TC_FAIL(TC_EINVAL, "tc_preprocess_components: a pair joins two components");
         hsrc.release();
         hdst.release();
         radix_sort_u64(&keys, &alt, P, 0, 2 * bits, al, st);
@@ -275,7 +319,10 @@ void preprocess(tc_graph* g, const int32_t* src_in, const int32_t* dst_in, int64
     size_t sz_tasks = align_up(sizeof(Task) * (size_t)std::max<int64_t>(m, 1));
     size_t sz_ctr = align_up(sizeof(unsigned long long) * CTR_COUNT) + align_up(sizeof(GraphView));
     size_t sz_tnew = align_up(8 * (size_t)std::max<int64_t>(n, 1));
-    g->arena_bytes = sz_off + sz_adj + sz_perm + sz_loff + sz_tasks + sz_ctr + sz_tnew;
+    size_t sz_comp = num_comps > 0 ? align_up(4 * (size_t)std::max<int64_t>(n, 1)) : 0;
+    size_t sz_ctot = num_comps > 0 ? align_up(8 * (size_t)num_comps) : 0;
+    sz_ctr += align_up(sizeof(GraphView));
+    g->arena_bytes = sz_off + sz_adj + sz_perm + sz_loff + sz_tasks + sz_ctr + sz_tnew + sz_comp + sz_ctot;
     g->arena = al.get(g->arena_bytes);
     char* a = static_cast<char*>(g->arena);
     g->off = a; a += sz_off;
@@ -285,8 +332,17 @@ void preprocess(tc_graph* g, const int32_t* src_in, const int32_t* dst_in, int64
     g->tasks = reinterpret_cast<Task*>(a); a += sz_tasks;
     g->counters = reinterpret_cast<unsigned long long*>(a);
     g->view = reinterpret_cast<GraphView*>(a + align_up(sizeof(unsigned long long) * CTR_COUNT));
+    g->view_comp = reinterpret_cast<GraphView*>(a + align_up(sizeof(unsigned long long) * CTR_COUNT) +
+                                                align_up(sizeof(GraphView)));
     a += sz_ctr;
     g->tnew = reinterpret_cast<uint64_t*>(a);
+    a += sz_tnew;
+    if (num_comps > 0) {
+        g->comp = reinterpret_cast<int32_t*>(a);
+        a += sz_comp;
+        g->comp_totals = reinterpret_cast<unsigned long long*>(a);
+        g->num_comps = num_comps;
+    }
 
     // a3 max degree, a4 relabel
     int maxdeg = 0;
@@ -316,6 +372,11 @@ void preprocess(tc_graph* g, const int32_t* src_in, const int32_t* dst_in, int64
     }
     g->stats.max_deg = maxdeg;
     deg.release();
+    if (num_comps > 0 && n > 0) {
+        Prof prof_("k_comp_new", st);
+        k_comp_new<<<grid_for(n, kT, G), kT, 0, st>>>(g->perm, n, vpre.get(), num_comps, g->comp);
+    }
+    TC_LAUNCH_CHECK();
 
     // a5 orient and build U
     Buf<int32_t> dplus(al, (size_t)std::max<int64_t>(n, 1));
@@ -424,6 +485,11 @@ void preprocess(tc_graph* g, const int32_t* src_in, const int32_t* dst_in, int64
         v.n = n;
         v.off64 = g->off64 ? 1 : 0;
         TC_CUDA(cudaMemcpyAsync(g->view, &v, sizeof(v), cudaMemcpyHostToDevice, st));
+        GraphView vc = v;
+        vc.tnew = nullptr;
+        vc.comp = g->comp;
+        vc.comp_totals = g->comp_totals;
+        TC_CUDA(cudaMemcpyAsync(g->view_comp, &vc, sizeof(vc), cudaMemcpyHostToDevice, st));
         TC_CUDA(cudaStreamSynchronize(st));
     }
 

@@ -9,12 +9,30 @@ constexpr int kSmallMaxOutdeg = 64;  // largest pivot row a warp unit takes
 constexpr int kMaxSlice = 4096;      // largest pivot slice a CTA unit tables
 constexpr int kMaxUnitTasks = 8192;  // 16-bit hit counters; a shared long-task queue
 
+// One RMAT request expanded on the device (same stream as tc_generate_rmat),
+// its ids shifted by vbase.
+struct RmatJob {
+    uint64_t key, A, B, C;
+    int64_t n, vbase;
+    int32_t scale;
+    uint32_t t1, t2, t3;
+};
+RmatJob make_rmat_job(uint64_t seed, int scale, int64_t n, uint32_t t1, uint32_t t2, uint32_t t3,
+                      int64_t vbase);
+void generate_rmat_multi(const RmatJob* jobs_dev, const int64_t* ppre_dev, int nreq, int64_t total,
+                         int32_t* src, int32_t* dst, cudaStream_t st);
+
 void tuning_defaults(tc_tuning* t);
 void tuning_resolve(const tc_tuning* in, tc_tuning* out);  // fills zeros, clamps
 bool tuning_equal(const tc_tuning& a, const tc_tuning& b);
 
 void preprocess(tc_graph* g, const int32_t* src, const int32_t* dst, int64_t P, uint32_t flags,
                 cudaStream_t st);
+// Same, with optional components (vpre_host: num_comps + 1 prefix of vertex
+// counts) checked and attached to the graph.
+void preprocess_with_components(tc_graph* g, const int32_t* src, const int32_t* dst, int64_t P,
+                                uint32_t flags, const int64_t* vpre_host, int32_t num_comps,
+                                cudaStream_t st);
 // Unit lists over the graphs of a view table (one graph, or a batch).
 struct UnitLists {
     void* mem = nullptr;
@@ -45,5 +63,12 @@ void launch_count(const GraphView* views_dev, const UnitLists& L, const tc_tunin
 void build_units(tc_graph* g, const tc_tuning& t, cudaStream_t st);
 void count(const tc_graph* g, const tc_tuning& t, uint64_t* total_dev, uint64_t* per_vertex_dev,
            cudaStream_t st);
+// Per-component totals of a graph preprocessed with components.
+void count_components(const tc_graph* g, const tc_tuning& t, uint64_t* comp_totals_dev,
+                      cudaStream_t st);
+// Marks the graph's vertices with components [vpre[c], vpre[c+1]) -> c and
+// checks that every pair stays inside one component (TC_EINVAL otherwise).
+void attach_components(tc_graph* g, const int32_t* src_dev, const int32_t* dst_dev, int64_t P,
+                       const int64_t* vpre_host, int32_t num_comps, cudaStream_t st);
 
 }  // namespace tc

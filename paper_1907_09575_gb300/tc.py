@@ -65,7 +65,9 @@ EXPORTS = ("tc_preprocess", "tc_count", "tc_triangles", "tc_graph_get_stats", "t
            "tc_tuning_default", "tc_last_error", "tc_generate_rmat", "tc_kernel_launches",
            "tc_profile_enable", "tc_profile_read", "tc_count_get_stats", "tc_triangles_static",
            "tc_batch_create", "tc_batch_count", "tc_batch_autotune", "tc_batch_get_count_stats",
-           "tc_batch_free", "tc_count_batch")
+           "tc_batch_free", "tc_count_batch", "tc_preprocess_components", "tc_count_components",
+           "tc_server_create", "tc_server_now", "tc_server_submit_rmat", "tc_server_poll",
+           "tc_server_drain", "tc_server_get_stats", "tc_server_free")
 
 TC_STATIC_MAX_PAIRS = 262144
 TC_STATIC_MAX_VERTICES = 65536
@@ -75,6 +77,31 @@ class CountStats(ctypes.Structure):
     _fields_ = [("triangles", ctypes.c_uint64), ("units", ctypes.c_uint64 * 2),
                 ("tasks", ctypes.c_uint64 * 2), ("probes", ctypes.c_uint64 * 2),
                 ("staged", ctypes.c_uint64 * 2)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("workers", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("max_tick_pairs", ctypes.c_int64),
+                ("device", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class RmatSpec(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("scale", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("n", ctypes.c_int64), ("num_pairs", ctypes.c_int64), ("t1", ctypes.c_uint32),
+                ("t2", ctypes.c_uint32), ("t3", ctypes.c_uint32), ("pad2", ctypes.c_uint32)]
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_int64), ("triangles", ctypes.c_uint64),
+                ("t_arrival", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("status", ctypes.c_int32),
+                ("tick_requests", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "completed", "failed", "pending", "ticks",
+                                               "bytes_in_flight", "peak_bytes_in_flight",
+                                               "busy_workers")]
 
 
 class KernelTime(ctypes.Structure):
@@ -111,6 +138,25 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tc_generate_rmat.restype = st
     lib.tc_count_get_stats.argtypes = [vp, ctypes.POINTER(CountStats), vp]
     lib.tc_count_get_stats.restype = st
+    lib.tc_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+    lib.tc_server_create.restype = st
+    lib.tc_server_now.argtypes = [vp]
+    lib.tc_server_now.restype = ctypes.c_double
+    lib.tc_server_submit_rmat.argtypes = [vp, ctypes.POINTER(RmatSpec), ctypes.c_double,
+                                          ctypes.POINTER(i64)]
+    lib.tc_server_submit_rmat.restype = st
+    lib.tc_server_poll.argtypes = [vp, ctypes.POINTER(ServerResult), i32, ctypes.POINTER(i32), i32]
+    lib.tc_server_poll.restype = st
+    lib.tc_server_drain.argtypes = [vp, i32]
+    lib.tc_server_drain.restype = st
+    lib.tc_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    lib.tc_server_get_stats.restype = st
+    lib.tc_server_free.argtypes = [vp]
+    lib.tc_server_free.restype = None
+    lib.tc_preprocess_components.argtypes = [vp, vp, i64, vp, i32, u32, vp, vp, ctypes.POINTER(vp)]
+    lib.tc_preprocess_components.restype = st
+    lib.tc_count_components.argtypes = [vp, vp, vp, vp]
+    lib.tc_count_components.restype = st
     lib.tc_batch_create.argtypes = [vp, i32, vp, vp, ctypes.POINTER(vp)]
     lib.tc_batch_create.restype = st
     lib.tc_batch_count.argtypes = [vp, vp, vp]
@@ -288,6 +334,68 @@ class Batch:
             pass
 
 
+class Server:
+    """tc_server_*: continuously batched counting of seeded RMAT requests."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, workers: int = 0, max_batch: int = 0,
+                 max_tick_pairs: int = 0, device: int = -1):
+        cfg = ServerConfig(hbm_budget_bytes, workers, max_batch, max_tick_pairs, device, 0)
+        h = ctypes.c_void_p(0)
+        _check(load().tc_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._buf = (ServerResult * 4096)()
+
+    def now(self) -> float:
+        return float(load().tc_server_now(self._h))
+
+    def submit_rmat(self, seed: int, scale: int, n: int, num_pairs: int,
+                    thresholds: Optional[tuple] = None, t_arrival: Optional[float] = None) -> int:
+        """Queue one request; returns its ticket (raises TCError on TC_EBUSY/EINVAL)."""
+        if thresholds is None:
+            from .inputs import rmat_thresholds
+            thresholds = rmat_thresholds()
+        spec = RmatSpec(seed & (2**64 - 1), scale, 0, n, num_pairs, *thresholds, 0)
+        t = ctypes.c_int64(-1)
+        _check(load().tc_server_submit_rmat(self._h, ctypes.byref(spec),
+                                            self.now() if t_arrival is None else t_arrival,
+                                            ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, wait_ms: int = 0) -> list:
+        """Finished results as dicts (ticket, triangles, times, status, tick_requests)."""
+        cnt = ctypes.c_int32(0)
+        out = []
+        while True:
+            _check(load().tc_server_poll(self._h, self._buf, len(self._buf), ctypes.byref(cnt),
+                                         wait_ms if not out else 0))
+            for i in range(cnt.value):
+                r = self._buf[i]
+                out.append({"ticket": int(r.ticket), "triangles": int(r.triangles),
+                            "t_arrival": r.t_arrival, "t_admit": r.t_admit, "t_done": r.t_done,
+                            "status": int(r.status), "tick_requests": int(r.tick_requests)})
+            if cnt.value < len(self._buf):
+                return out
+
+    def drain(self, timeout_ms: int = 600000) -> None:
+        _check(load().tc_server_drain(self._h, timeout_ms))
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(load().tc_server_get_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+    def free(self) -> None:
+        if self._h.value:
+            load().tc_server_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
 def count_batch(graphs, tuning: Optional[Tuning] = None, stream=None):
     """tc_count_batch: one-shot batched count; returns a CUDA int64 tensor."""
     import torch
@@ -319,6 +427,38 @@ def preprocess(src, dst, n: int, offsets: Optional[int] = None, stream=None,
                                 ctypes.byref(allocator) if allocator is not None else None,
                                 _stream_ptr(stream), ctypes.byref(h)))
     return Graph(h.value, n)
+
+
+def preprocess_components(src, dst, vertex_prefix, offsets: Optional[int] = None,
+                          stream=None) -> Graph:
+    """tc_preprocess_components: the disjoint union of graphs whose vertex
+    ranges are given by ``vertex_prefix`` (num_comps + 1 ints, starting at 0)."""
+    ps, dev_s = _ptr(src)
+    pd, dev_d = _ptr(dst)
+    assert dev_s == dev_d
+    vp_ = np.ascontiguousarray(np.asarray(vertex_prefix, dtype=np.int64))
+    flags = TC_INPUT_ON_DEVICE if dev_s else 0
+    if offsets == 32:
+        flags |= TC_OFFSETS_32
+    elif offsets == 64:
+        flags |= TC_OFFSETS_64
+    h = ctypes.c_void_p(0)
+    _check(load().tc_preprocess_components(ps, pd, int(src.shape[0]), vp_.ctypes.data,
+                                           vp_.size - 1, flags, None, _stream_ptr(stream),
+                                           ctypes.byref(h)))
+    g = Graph(h.value, int(vp_[-1]))
+    g.num_comps = vp_.size - 1
+    return g
+
+
+def count_components(g: Graph, tuning: Optional[Tuning] = None, out=None, stream=None):
+    """tc_count_components: per-component totals as a CUDA int64 tensor."""
+    import torch
+    if out is None:
+        out = torch.empty(g.num_comps, dtype=torch.int64, device="cuda")
+    _check(load().tc_count_components(g._h, ctypes.byref(tuning) if tuning is not None else None,
+                                      out.data_ptr(), _stream_ptr(stream)))
+    return out
 
 
 def triangles(src: np.ndarray, dst: np.ndarray, n: int, per_vertex: bool = False,
