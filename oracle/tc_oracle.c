@@ -231,6 +231,14 @@ int tc_oracle_vertex_triangles(const int32_t* src, const int32_t* dst, int64_t n
     if (ns < 0 || ns > 64 || n < 0 || num_pairs < 0) return -1;
     for (int64_t s = 0; s < ns; ++s)
         if (samples[s] < 0 || samples[s] >= n) return -1;
+    /* which sampled vertices each vertex is: vertex -> bitmask of samples */
+    slot_t who[256];
+    for (int64_t q = 0; q < 256; ++q) who[q].key = -1;
+    for (int64_t s = 0; s < ns; ++s) {
+        int64_t p = hash_find(who, 256, samples[s]);
+        if (who[p].key == -1) { who[p].key = samples[s]; who[p].mask = 0; }
+        who[p].mask |= 1ULL << s;
+    }
     /* scan 1: neighbour sets, kept as vertex -> bitmask of samples adjacent to it */
     int64_t cap = 1024, used = 0;
     slot_t* tab = (slot_t*)malloc((size_t)cap * sizeof(slot_t));
@@ -239,9 +247,13 @@ int tc_oracle_vertex_triangles(const int32_t* src, const int32_t* dst, int64_t n
         int64_t a = src[e], b = dst[e];
         if (a < 0 || a >= n || b < 0 || b >= n) { free(tab); return -1; }
         if (a == b) continue;
+        int64_t pa = hash_find(who, 256, a), pb = hash_find(who, 256, b);
+        uint64_t sa = who[pa].key == a ? who[pa].mask : 0;   /* samples equal to a */
+        uint64_t sb = who[pb].key == b ? who[pb].mask : 0;
+        if (!(sa | sb)) continue;
         for (int64_t s = 0; s < ns; ++s) {
             int64_t x = -1;
-            if (a == samples[s]) x = b; else if (b == samples[s]) x = a;
+            if ((sa >> s) & 1ULL) x = b; else if ((sb >> s) & 1ULL) x = a;
             if (x < 0) continue;
             if (2 * (used + 1) > cap) {
                 int64_t ncap = cap * 2;

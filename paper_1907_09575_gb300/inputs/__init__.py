@@ -141,7 +141,7 @@ def chung_lu_weights(n: int, gamma: float = 2.1, mean_degree: float = 40.0,
         hi *= 2.0
         if hi > 1e300:
             raise ValueError("mean degree unreachable under the cap")
-    for _ in range(200):
+    for _ in range(64):   # halves the bracket each time: far below one ulp of c
         mid = 0.5 * (lo + hi)
         if mean_w(mid) < mean_degree:
             lo = mid

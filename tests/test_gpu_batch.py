@@ -97,3 +97,29 @@ def test_batch_autotune_keeps_counts(tc):
         x.free()
     for g in graphs:
         g.free()
+
+
+def test_components_union_matches_each_graph(tc):
+    """A disjoint union preprocessed once, counted per component."""
+    specs = small_batch(5, 30, max_log_n=11)
+    srcs, dsts, vpre, want = [], [], [0], []
+    for sp in specs:
+        s, d = sp.generate()
+        want.append(oracle.count(s, d, sp.n))
+        srcs.append(s.astype(np.int64) + vpre[-1])
+        dsts.append(d.astype(np.int64) + vpre[-1])
+        vpre.append(vpre[-1] + sp.n)
+    s = np.concatenate(srcs).astype(np.int32)
+    d = np.concatenate(dsts).astype(np.int32)
+    for dev in (False, True):
+        a, b = (torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda()) if dev else (s, d)
+        g = tc.preprocess_components(a, b, vpre)
+        assert tc.count_components(g).cpu().numpy().tolist() == want
+        assert g.count() == sum(want)          # the plain count of the union
+        g.free()
+    # a pair across two components is rejected
+    bad_s = np.concatenate([s, np.array([0], np.int32)])
+    bad_d = np.concatenate([d, np.array([vpre[-1] - 1], np.int32)])
+    with pytest.raises(tc.TCError) as ei:
+        tc.preprocess_components(bad_s, bad_d, vpre)
+    assert ei.value.status == tc.TC_EINVAL
