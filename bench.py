@@ -186,13 +186,13 @@ def traffic_for(kernel: str, workload: str, units: float):
     return per_unit * units, f"ncu capture of {e['case']} scaled by units ({e['unit_name']})"
 
 
-def alg_bytes_count(kstats: dict, idx: int, off_bytes: int, per_vertex: bool) -> float:
-    """Algorithmic bytes of one count kernel launch (index 0 warp kernel, 1 CTA
-    kernel): per unit its record (24 B) and the pivot row bounds (2 offsets);
-    per staged pivot entry 4 B; per task its record (16 B); per probe the 4-B
-    entry of U_i read.  Per-vertex flushes are not counted (atomics)."""
-    return (kstats["units"][idx] * (24 + 2 * off_bytes) + 4 * kstats["staged"][idx]
-            + 16 * kstats["tasks"][idx] + 4 * kstats["probes"][idx])
+def alg_bytes_count(kstats: dict, off_bytes: int) -> float:
+    """Algorithmic bytes of one count kernel launch (warp and CTA units): per
+    unit its record (32 B) and the pivot row bounds (2 offsets); per staged
+    pivot entry 4 B; per task its record (16 B); per probe the 4-B entry of
+    U_i read.  Per-vertex flushes are not counted (atomics)."""
+    return (sum(kstats["units"]) * (32 + 2 * off_bytes) + 4 * sum(kstats["staged"])
+            + 16 * sum(kstats["tasks"]) + 4 * sum(kstats["probes"]))
 
 
 # ----------------------------------------------------------------------------
@@ -200,37 +200,56 @@ def alg_bytes_count(kstats: dict, idx: int, off_bytes: int, per_vertex: bool) ->
 # ----------------------------------------------------------------------------
 
 def run_reference(args, wl):
+    """The CPU oracle (single thread) on a bounded sample of the same
+    workload, each step a few seconds of work, same metric and unit."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle
     from paper_1907_09575_gb300 import inputs
     oracle.build()
-    scale = args.cpu_sample_scale - 1   # per step: a sample the oracle counts in a few seconds
-    spec = inputs.rmat_graph(args.seed, scale, 16)
-    src, dst = spec.generate()
-    times, m = [], 0
+    kind = wl["kind"]
+    unit, metric = "edges/s", "undirected edges/sec (exact triangle count)"
+    if kind == "rmat":
+        scale = min(wl["scale"], args.cpu_sample_scale - 1)
+        specs = [inputs.rmat_graph(args.seed, scale, wl["edge_factor"])]
+        sample = (f"RMAT scale {scale}, edge factor {wl['edge_factor']} per step"
+                  + (" (the whole workload)" if scale == wl["scale"] else ""))
+    elif kind == "chung_lu":
+        specs = [inputs.chung_lu_graph(args.seed, n=1_000_000, gamma=wl["gamma"],
+                                       mean_degree=wl["mean_degree"], wmax=wl["wmax"])]
+        sample = "Chung-Lu with the same law on 1,000,000 vertices per step"
+    elif kind == "batch":
+        specs = [inputs.batch_member(args.seed, k) for k in range(64)]
+        sample = "the first 64 graphs of the batch per step"
+    else:
+        unit, metric = "requests/s", "served exact triangle counts: throughput with p50/p99 latency"
+        specs = [inputs.serve_request(args.seed, r) for r in range(24)]
+        sample = "the first 24 requests of the stream per step, counted one after another"
+    data = [(sp, sp.generate()) for sp in specs]
+    times, work = [], 0
     for it in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        total, st = oracle.count(src, dst, spec.n, stats=True)
+        w = 0
+        for sp, (src, dst) in data:
+            total, st = oracle.count(src, dst, sp.n, stats=True)
+            w += st["m"] if unit == "edges/s" else 1
         dt = time.perf_counter() - t0
-        m = st["m"]
+        work = w
         if it >= args.warmup:
             times.append(dt)
     step_s = sum(times) / len(times)
-    value = m / step_s
-    sample = (f"RMAT scale {scale}, edge factor 16 ({spec.num_pairs} pairs, m={m}) per step: "
-              f"the oracle's full preprocess+count, single thread")
+    value = work / step_s
+    sample += f" ({work} {'edges' if unit == 'edges/s' else 'requests'}); oracle preprocess+count, single thread"
     line = {
-        "impl": "reference", "metric": "undirected edges/sec (exact triangle count)",
-        "value": value, "unit": "edges/s", "n_gpus": ws, "steps": args.steps,
+        "impl": "reference", "metric": metric,
+        "value": value, "unit": unit, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": args.workload, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
                          "sample": sample},
-        "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 0},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
@@ -358,18 +377,17 @@ def run_ours(args, wl):
     top = max(prof.items(), key=lambda kv: kv[1][1])
     kname, (klaunch, kms) = top
     roof = None
-    if kname in ("k_count_large", "k_count_small"):
-        idx = 1 if kname == "k_count_large" else 0
-        b_launch = alg_bytes_count(kst, idx, facts["offset_bytes"], wl["per_vertex"])
+    if kname == "k_count":
+        b_launch = alg_bytes_count(kst, facts["offset_bytes"])
         avg_ms = kms / klaunch
         achieved = b_launch / (avg_ms / 1e3) / 1e9
-        traffic, tnote = traffic_for(kname, args.workload, kst["probes"][idx])
+        traffic, tnote = traffic_for(kname, args.workload, sum(kst["probes"]))
         roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                 "traffic_note": tnote, "peak_source": peak_src,
                 "alg_bytes_per_launch": b_launch, "avg_launch_ms": avg_ms,
                 "share_of_step_kernel_time": kms / step_kernel_ms,
-                "probes_per_launch": kst["probes"][idx]}
+                "probes_per_launch": sum(kst["probes"])}
     else:
         roof = {"kernel": kname, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
                 "frac": None, "traffic": None, "peak_source": peak_src,
@@ -548,8 +566,7 @@ def run_batch(args, wl):
 
     hbm, peak_src = peaks()
     kb = prof.get("k_count_batch", (args.steps, ms * args.steps))
-    b_launch = (sum(kst["units"]) * 40 + 4 * sum(kst["staged"]) + 16 * sum(kst["tasks"])
-                + 4 * sum(kst["probes"]))
+    b_launch = alg_bytes_count(kst, wl["offsets"] // 8)
     achieved = b_launch / (kb[1] / kb[0] / 1e3) / 1e9
     roof = {"kernel": "k_count (batched, one captured launch)", "bound": "hbm",
             "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
