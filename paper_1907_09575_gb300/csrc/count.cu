@@ -35,6 +35,9 @@ namespace {
 #ifndef TC_PREFETCH
 #define TC_PREFETCH 1          // prefetch the next long task's record and tail head
 #endif
+#ifndef TC_DEFER_CREDIT
+#define TC_DEFER_CREDIT 0      // all lookups of an unrolled step before its per-entry credits
+#endif
 #ifndef TC_LARGE_MINB
 #define TC_LARGE_MINB 4        // CTAs per SM the CTA kernel's registers must allow
 #endif
@@ -43,7 +46,10 @@ constexpr int kSmallWarps = 8;
 constexpr int kSmallThreads = kSmallWarps * 32;
 constexpr int kGrab = 4;          // warp units popped per queue access
 constexpr int kEmpty = -1;
-constexpr int kUnroll = 4;        // independent loads in flight per lane
+#ifndef TC_UNROLL
+#define TC_UNROLL 4
+#endif
+constexpr int kUnroll = TC_UNROLL;   // independent loads in flight per lane
 // warp unit table region: 128 hash slots, or a 128-word bitmap (4096 labels)
 // plus its 128 16-bit rank prefixes
 constexpr int kSmallBitWords = 128;
@@ -224,9 +230,21 @@ __device__ __forceinline__ unsigned warp_walk_tail_scalar(int64_t st, int L, con
             const int q = q0 + 32 * u + lane;
             k[u] = (q < L) ? __ldg(&adj[st + q]) : -1;
         }
+#if TC_DEFER_CREDIT
+        int r[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) r[u] = (k[u] >= 0) ? T.template find<PV>(k[u]) : -1;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (r[u] >= 0) {
+                ++mine;
+                if (PV) count_hit(cnt, r[u]);
+            }
+#else
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u)
             if (k[u] >= 0) probe_one<PV>(T, k[u], cnt, mine);
+#endif
     }
     hits += mine;
     if (!PV) return 0;
@@ -324,17 +342,19 @@ __device__ __forceinline__ void warp_probe_group(const Task* __restrict__ tasks,
             const int q = qb + lane;
             k[u] = (q < total) ? __ldg(&adj[s_base[o] + q]) : -1;
         }
+        int r[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) r[u] = (k[u] >= 0) ? T.template find<PV>(k[u]) : -1;
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            const int r = (k[u] >= 0) ? T.template find<PV>(k[u]) : -1;
-            const bool hit = r >= 0;
+            const bool hit = r[u] >= 0;
             hits += hit ? 1 : 0;
             if (PV) {
                 const unsigned hm = __ballot_sync(0xffffffffu, hit);
                 const int qb = q0 + 32 * u;
                 const int plo = max(excl - qb, 0), phi = min(excl + slen - qb, 32);
                 if (sv && plo < phi) c += __popc(hm & bit_range(plo, phi));
-                if (hit) count_hit(cnt, r);
+                if (hit) count_hit(cnt, r[u]);
             }
         }
     }
