@@ -1,14 +1,17 @@
 // Stable LSD radix sort of 64-bit keys on a bit range, 8-bit digits.
 //
-// Per digit: (1) every tile of kTile keys counts its digits into per-warp
-// shared histograms (plain shared atomics; a warp whose keys all share one
-// digit adds once), written digit-major to the (digit, tile) table; (2) one
-// exclusive scan of that table gives each (digit, tile) its output offset;
-// (3) every tile loads its keys into shared memory, ranks them stably (warp w
-// owns a contiguous segment; the lanes holding the same digit are found with
-// one ballot per digit bit, and a running per-warp counter orders the
-// rounds), permutes them into digit order in shared memory and writes each
-// digit run out contiguously.
+// One kernel first counts every digit position of every key (LSD passes only
+// permute keys, so all passes' global digit counts are known up front).  Then
+// each pass is one kernel: a tile of kTile keys, taken in launch order from a
+// tile counter, is staged in shared memory and ranked stably (warp w owns a
+// contiguous segment; the lanes holding the same digit are found with one
+// ballot per digit bit, and a running per-warp counter orders the rounds);
+// the tile publishes its digit counts and finds, per digit, how many keys
+// earlier tiles hold by looking back over their published counts (decoupled
+// look-back: a tile that has its inclusive prefix publishes it, so the walk
+// stops there); it then permutes its keys into digit order in shared memory
+// and writes each digit run out contiguously.  Look-back waits are bounded:
+// past the bound the pass records an error and the sort reports TC_ETIMEOUT.
 #include "common.cuh"
 
 namespace tc {
@@ -26,41 +29,6 @@ __device__ __forceinline__ unsigned digit_of(uint64_t k, int shift, unsigned mas
     return (unsigned)(k >> shift) & mask;
 }
 
-__global__ void __launch_bounds__(kThreads) k_hist(const uint64_t* __restrict__ keys, int64_t count,
-                                                   int shift, unsigned mask,
-                                                   int64_t* __restrict__ H, int64_t nblocks) {
-    __shared__ unsigned hist[kWarps][kRadix];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&hist[0][0])[i] = 0;
-    __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)w * kSeg;
-    uint64_t k[kRounds];
-#pragma unroll
-    for (int r = 0; r < kRounds; ++r) {
-        const int64_t idx = base + r * 32 + lane;
-        k[r] = idx < count ? keys[idx] : 0;
-    }
-#pragma unroll
-    for (int r = 0; r < kRounds; ++r) {
-        const bool valid = base + r * 32 + lane < count;
-        const unsigned d = digit_of(k[r], shift, mask);
-        const unsigned d0 = __shfl_sync(0xffffffffu, d, 0);
-        const unsigned vm = __ballot_sync(0xffffffffu, valid);
-        if (__all_sync(0xffffffffu, !valid || d == d0)) {
-            if (lane == 0 && vm) atomicAdd(&hist[w][d0], (unsigned)__popc(vm));
-        } else if (valid) {
-            atomicAdd(&hist[w][d], 1u);
-        }
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d <= (int)mask; d += kThreads) {
-        unsigned s = 0;
-#pragma unroll
-        for (int q = 0; q < kWarps; ++q) s += hist[q][d];
-        H[(int64_t)d * nblocks + blockIdx.x] = s;
-    }
-}
-
 // Lanes of the warp whose digit equals this lane's (one ballot per digit bit).
 __device__ __forceinline__ unsigned digit_peers(unsigned d, int nbits, unsigned valid_mask) {
     unsigned peers = valid_mask;
@@ -75,31 +43,96 @@ __device__ __forceinline__ unsigned digit_peers(unsigned d, int nbits, unsigned 
     return peers;
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_scatter(const uint64_t* __restrict__ in,
-                                                         uint64_t* __restrict__ out, int64_t count,
-                                                         int shift, int nbits,
-                                                         const int64_t* __restrict__ H,
-                                                         int64_t nblocks) {
+constexpr int kMaxPasses = 8;
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagPre = 2ull << 62;
+constexpr unsigned long long kValMask = (1ull << 62) - 1ull;
+constexpr long kSpinLimit = 1l << 24;
+
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Global digit counts of every pass: hist[pass][digit], bits [lo, hi).
+__global__ void __launch_bounds__(kThreads) k_digit_hist(const uint64_t* __restrict__ keys,
+                                                         int64_t count, int lo, int npass, int hi,
+                                                         unsigned long long* __restrict__ hist) {
+    __shared__ unsigned h[kMaxPasses][kRadix];
+    for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += kThreads) (&h[0][0])[i] = 0;
+    __syncthreads();
+    for (int64_t base = blockIdx.x * (int64_t)kThreads; base < count; base += (int64_t)gridDim.x * kThreads) {
+        const int64_t idx = base + threadIdx.x;
+        const bool valid = idx < count;
+        const uint64_t k = valid ? keys[idx] : 0;
+        for (int p = 0; p < npass; ++p) {
+            const int shift = lo + 8 * p;
+            const unsigned mask = (1u << min(8, hi - shift)) - 1u;
+            const unsigned d = digit_of(k, shift, mask);
+            const unsigned d0 = __shfl_sync(0xffffffffu, d, 0);
+            const unsigned vm = __ballot_sync(0xffffffffu, valid);
+            if (__all_sync(0xffffffffu, !valid || d == d0)) {
+                if ((threadIdx.x & 31) == 0 && vm) atomicAdd(&h[p][d0], (unsigned)__popc(vm));
+            } else if (valid) {
+                atomicAdd(&h[p][d], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < npass * kRadix; i += kThreads) {
+        const unsigned c = (&h[0][0])[i];
+        if (c) atomicAdd(&hist[i], (unsigned long long)c);
+    }
+}
+
+// hist[pass][digit] -> exclusive prefix over digits, per pass (one warp per pass).
+__global__ void k_digit_offsets(unsigned long long* __restrict__ hist, int npass) {
+    const int p = blockIdx.x;
+    if (p >= npass) return;
+    unsigned long long* h = hist + (size_t)p * kRadix;
+    if (threadIdx.x == 0) {
+        unsigned long long run = 0;
+        for (int d = 0; d < kRadix; ++d) {
+            const unsigned long long c = h[d];
+            h[d] = run;
+            run += c;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint64_t* __restrict__ in,
+                                                          uint64_t* __restrict__ out, int64_t count,
+                                                          int shift, int nbits,
+                                                          const unsigned long long* __restrict__ goff,
+                                                          unsigned long long* status,
+                                                          unsigned* tile_ctr, int* err) {
     __shared__ uint64_t stage[kTile];
     __shared__ unsigned short rank_s[kTile];
-    __shared__ unsigned short wcnt[kWarps][kRadix];   // counts, then per-warp exclusive prefix
-    __shared__ unsigned dstart[kRadix];               // tile-local start of each digit run
+    __shared__ unsigned short wcnt[kWarps][kRadix];
+    __shared__ unsigned dstart[kRadix];
     __shared__ unsigned wsum[kWarps];
+    __shared__ unsigned long long s_goff[kRadix];
+    __shared__ int s_tile;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const unsigned mask = (1u << nbits) - 1u;
-    const int64_t tbase = (int64_t)blockIdx.x * kTile;
-    const int valid_in_tile = (int)min64((int64_t)kTile, count - tbase);
-
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_ctr, 1u);
     for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const int tile = s_tile;
+    const int64_t tbase = (int64_t)tile * kTile;
+    const int valid_in_tile = (int)min64((int64_t)kTile, count - tbase);
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
         const int p = k * kThreads + threadIdx.x;
         if (p < valid_in_tile) stage[p] = in[tbase + p];
     }
     __syncthreads();
-
-    // stable ranks within each warp's segment
     const int seg = w * kSeg;
 #pragma unroll 4
     for (int r = 0; r < kRounds; ++r) {
@@ -117,16 +150,45 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(const uint64_t* __restr
         __syncwarp();
     }
     __syncthreads();
-    // per-warp exclusive prefix per digit, and digit totals
     unsigned tot = 0;
     {
-        const int d = threadIdx.x;   // kThreads == kRadix
+        const int d = threadIdx.x;
 #pragma unroll
         for (int q = 0; q < kWarps; ++q) {
             const unsigned c = wcnt[q][d];
             wcnt[q][d] = (unsigned short)tot;
             tot += c;
         }
+    }
+    // publish this tile's count of digit d and look back for the keys of
+    // digit d in earlier tiles
+    {
+        const int d = threadIdx.x;
+        unsigned long long* my = status + (size_t)tile * kRadix + d;
+        unsigned long long excl = 0;
+        if (tile == 0) {
+            st_relaxed(my, kFlagPre | (unsigned long long)tot);
+        } else {
+            st_relaxed(my, kFlagAgg | (unsigned long long)tot);
+            for (int p = tile - 1; p >= 0; --p) {
+                const unsigned long long* q = status + (size_t)p * kRadix + d;
+                unsigned long long v = ld_relaxed(q);
+                long spins = 0;
+                while ((v >> 62) == 0) {
+                    if (++spins > kSpinLimit) {
+                        atomicOr(err, 4);
+                        v = kFlagPre;
+                        break;
+                    }
+                    __nanosleep(32);
+                    v = ld_relaxed(q);
+                }
+                excl += v & kValMask;
+                if ((v >> 62) == 2) break;
+            }
+            st_relaxed(my, kFlagPre | (excl + tot));
+        }
+        s_goff[d] = goff[d] + excl;
     }
     unsigned inc = tot;
 #pragma unroll
@@ -140,7 +202,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(const uint64_t* __restr
     for (int q = 0; q < w; ++q) before += wsum[q];
     dstart[threadIdx.x] = before + inc - tot;
     __syncthreads();
-    // permute into digit order inside the tile
     uint64_t key[kItems];
     unsigned pos[kItems];
 #pragma unroll
@@ -165,7 +226,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(const uint64_t* __restr
         if (p < valid_in_tile) {
             const uint64_t kk = stage[p];
             const unsigned d = digit_of(kk, shift, mask);
-            out[H[(int64_t)d * nblocks + blockIdx.x] + (p - (int)dstart[d])] = kk;
+            out[s_goff[d] + (uint64_t)(p - (int)dstart[d])] = kk;
         }
     }
 }
@@ -175,28 +236,44 @@ __global__ void __launch_bounds__(kThreads, 4) k_scatter(const uint64_t* __restr
 void radix_sort_u64(uint64_t** keys, uint64_t** alt, int64_t count, int lo, int hi, Alloc& al,
                     cudaStream_t st) {
     if (count <= 1 || hi <= lo) return;
-    const int64_t nblocks = (count + kTile - 1) / kTile;
-    Buf<int64_t> H(al, (size_t)(kRadix * nblocks));
-    for (int shift = lo; shift < hi; shift += 8) {
+    const int64_t ntiles = (count + kTile - 1) / kTile;
+    const int npass = (hi - lo + 7) / 8;
+    // [hist: kMaxPasses x 256 u64][tile counters: kMaxPasses u32][error flag]
+    Buf<unsigned long long> hist(al, (size_t)kMaxPasses * kRadix + 8);
+    Buf<unsigned long long> status(al, (size_t)ntiles * kRadix);
+    unsigned* ctrs = reinterpret_cast<unsigned*>(hist.get() + (size_t)kMaxPasses * kRadix);
+    int* err = reinterpret_cast<int*>(ctrs + kMaxPasses);
+    TC_CUDA(cudaMemsetAsync(hist.get(), 0, sizeof(unsigned long long) * ((size_t)kMaxPasses * kRadix + 8), st));
+    {
+        Prof prof_("k_digit_hist", st);
+        k_digit_hist<<<grid_for(count, kThreads, (int64_t)num_sms() * 8), kThreads, 0, st>>>(
+            *keys, count, lo, npass, hi, hist.get());
+    }
+    TC_LAUNCH_CHECK();
+    {
+        Prof prof_("k_digit_offsets", st);
+        k_digit_offsets<<<npass, 32, 0, st>>>(hist.get(), npass);
+    }
+    TC_LAUNCH_CHECK();
+    for (int p = 0; p < npass; ++p) {
+        const int shift = lo + 8 * p;
         const int nbits = min(8, hi - shift);
-        const unsigned mask = (1u << nbits) - 1u;
-        const int64_t rows = (int64_t)(mask + 1) * nblocks;
+        TC_CUDA(cudaMemsetAsync(status.get(), 0, sizeof(unsigned long long) * (size_t)ntiles * kRadix, st));
         {
-            Prof prof_("k_hist", st);
-            k_hist<<<(unsigned)nblocks, kThreads, 0, st>>>(*keys, count, shift, mask, H.get(), nblocks);
-        }
-        TC_LAUNCH_CHECK();
-        exclusive_scan_i64(H.get(), H.get(), rows, nullptr, al, st);
-        {
-            Prof prof_("k_scatter", st);
-            k_scatter<<<(unsigned)nblocks, kThreads, 0, st>>>(*keys, *alt, count, shift, nbits, H.get(),
-                                                              nblocks);
+            Prof prof_("k_onesweep", st);
+            k_onesweep<<<(unsigned)ntiles, kThreads, 0, st>>>(*keys, *alt, count, shift, nbits,
+                                                              hist.get() + (size_t)p * kRadix,
+                                                              status.get(), ctrs + p, err);
         }
         TC_LAUNCH_CHECK();
         uint64_t* t = *keys;
         *keys = *alt;
         *alt = t;
     }
+    int herr = 0;
+    TC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    if (herr) TC_FAIL(TC_ETIMEOUT, "radix sort: a look-back wait ran past its bound");
 }
 
 }  // namespace tc
