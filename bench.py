@@ -159,14 +159,17 @@ def peaks() -> tuple[float, str]:
         return FALLBACK_HBM_GBS, "fallback 6.8 TB/s"
 
 
-def source_digest() -> str:
+KERNEL_SOURCES = {"k_count": ("count.cu", "common.cuh", "tc_internal.cuh")}
+
+
+def source_digest(kernel: str = "k_count") -> str:
+    """Digest of the source files a kernel is compiled from."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1907_09575_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            h.update(name.encode())
-            h.update(open(os.path.join(csrc, name), "rb").read())
+    for name in KERNEL_SOURCES.get(kernel, ()):
+        h.update(name.encode())
+        h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -180,7 +183,7 @@ def traffic_for(kernel: str, workload: str, units: float):
     except (OSError, ValueError):
         return None, "no ncu capture committed"
     e = rec.get(kernel)
-    if not e or e.get("source_digest") != source_digest():
+    if not e or e.get("source_digest") != source_digest(kernel):
         return None, "kernel changed since the ncu capture" if e else "no capture of this kernel"
     per_unit = e["dram_bytes"] / max(e["units"], 1)
     return per_unit * units, f"ncu capture of {e['case']} scaled by units ({e['unit_name']})"
@@ -486,17 +489,21 @@ def run_batch(args, wl):
     seed = args.seed + rank
     t0 = time.perf_counter()
     graphs, pairs, ms_list = [], 0, []
-    host_pairs = []   # kept pinned for the end-to-end pass
+    host_pairs = []   # for the end-to-end pass: all graphs as one disjoint union
+    vprefix = [0]
     for k in range(ngraphs):
         spec = inputs.batch_member(seed, k)
         hs, hd = spec.generate()
         pairs += hs.size
         if not args.no_e2e:
-            ps = torch.from_numpy(hs).pin_memory()
-            pd = torch.from_numpy(hd).pin_memory()
-            host_pairs.append((ps, pd, spec.n))
+            host_pairs.append((hs.astype(np.int64) + vprefix[-1], hd.astype(np.int64) + vprefix[-1]))
+        vprefix.append(vprefix[-1] + spec.n)
         graphs.append(tc.preprocess(torch.from_numpy(hs).cuda(), torch.from_numpy(hd).cuda(),
                                     spec.n, offsets=wl["offsets"]))
+    if not args.no_e2e:
+        union_s = torch.from_numpy(np.concatenate([a for a, _ in host_pairs]).astype(np.int32)).pin_memory()
+        union_d = torch.from_numpy(np.concatenate([b for _, b in host_pairs]).astype(np.int32)).pin_memory()
+        host_pairs = None
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     facts = [g.stats() for g in graphs]
@@ -579,18 +586,17 @@ def run_batch(args, wl):
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        for _ in range(max(1, min(args.steps, 2))):
-            gs2 = [tc.preprocess(ps.numpy(), pd.numpy(), n, offsets=wl["offsets"])
-                   for ps, pd, n in host_pairs]
-            out = tc.count_batch(gs2, tuning=tuning)
-            host_totals = out.cpu()
-            for g in gs2:
-                g.free()
-        e2e_s = (time.perf_counter() - t0) / max(1, min(args.steps, 2))
+        us_np, ud_np = union_s.numpy(), union_d.numpy()
+        for _ in range(args.steps):
+            gu = tc.preprocess_components(us_np, ud_np, vprefix)
+            host_totals = tc.count_components(gu).cpu()
+            gu.free()
+        e2e_s = (time.perf_counter() - t0) / args.steps
         assert torch.equal(host_totals.cuda(), totals)
         e2e = {"value": m_tot / e2e_s, "unit": "edges/s", "ms_per_step": e2e_s * 1e3,
                "h2d_bytes_per_step": 8 * pairs, "d2h_bytes_per_step": 8 * ngraphs,
-               "call": "tc_preprocess per graph from pinned host pairs, tc_count_batch, totals to host"}
+               "call": "tc_preprocess_components on the pinned host pairs of all graphs (one "
+                       "disjoint union), tc_count_components, totals to host"}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
