@@ -35,6 +35,9 @@ namespace {
 #ifndef TC_PREFETCH
 #define TC_PREFETCH 1          // prefetch the next long task's record and tail head
 #endif
+#ifndef TC_FULLSTEP
+#define TC_FULLSTEP 1          // unchecked full steps in the long-tail walk
+#endif
 #ifndef TC_DEFER_CREDIT
 #define TC_DEFER_CREDIT 0      // all lookups of an unrolled step before its per-entry credits
 #endif
@@ -222,29 +225,29 @@ template <bool PV, class Tab>
 __device__ __forceinline__ unsigned warp_walk_tail_scalar(int64_t st, int L, const int32_t* __restrict__ adj,
                                                           const Tab& T, unsigned* cnt, uint64_t& hits) {
     const int lane = threadIdx.x & 31;
+    const int32_t* __restrict__ p = adj + st + lane;
     unsigned mine = 0;
-    for (int q0 = 0; q0 < L; q0 += 32 * kUnroll) {
+    int q0 = 0;
+#if TC_FULLSTEP
+    // full steps: every lane reads kUnroll entries, no bounds checks
+    for (; q0 + 32 * kUnroll <= L; q0 += 32 * kUnroll) {
+        int k[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) k[u] = __ldg(p + q0 + 32 * u);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) probe_one<PV>(T, k[u], cnt, mine);
+    }
+#endif
+    for (; q0 < L; q0 += 32 * kUnroll) {
         int k[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const int q = q0 + 32 * u + lane;
-            k[u] = (q < L) ? __ldg(&adj[st + q]) : -1;
+            k[u] = (q < L) ? __ldg(p + q0 + 32 * u) : -1;
         }
-#if TC_DEFER_CREDIT
-        int r[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) r[u] = (k[u] >= 0) ? T.template find<PV>(k[u]) : -1;
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-            if (r[u] >= 0) {
-                ++mine;
-                if (PV) count_hit(cnt, r[u]);
-            }
-#else
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u)
             if (k[u] >= 0) probe_one<PV>(T, k[u], cnt, mine);
-#endif
     }
     hits += mine;
     if (!PV) return 0;
