@@ -251,3 +251,16 @@ def test_one_shot_host_call(tc):
     total, t = tc.triangles(s, d, spec.n, per_vertex=True)
     assert total == want and np.array_equal(t, want_t)
     assert tc.triangles(s, d, spec.n) == want
+
+
+@pytest.mark.parametrize("num", [1, 2, 4095, 4096, 4097, 8191, 8192, 12289, 65535, 65537, 262143])
+def test_sort_tile_boundaries(tc, num):
+    """Pair counts around multiples of the 4096-key sort tile (one tile, a
+    ragged last tile, many tiles) for random and RMAT-shaped graphs."""
+    rng = np.random.default_rng(num)
+    n = int(max(2, min(num, 5000)))
+    s = rng.integers(0, n, size=num).astype(np.int32)
+    d = rng.integers(0, n, size=num).astype(np.int32)
+    check(tc, s, d, n)
+    hs, hd = inputs.rmat(num, 12, num)
+    check(tc, hs, hd, 4096, offsets=64)
