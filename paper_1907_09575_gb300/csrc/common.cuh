@@ -131,9 +131,12 @@ void exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t count,
                                int64_t* total_dev, Alloc& al, cudaStream_t st);
 
 // Stable LSD radix sort of 64-bit keys on bits [lo, hi).  Sorted keys end up
-// in *keys (the two buffers may be swapped).  count <= 2^31 - 1.
+// in *keys (the two buffers may be swapped).  count <= 2^31 - 1.  With
+// err_dev, a look-back timeout ORs 4 into *err_dev and the call returns
+// without synchronising; without it, the call synchronises and throws
+// TC_ETIMEOUT itself.
 void radix_sort_u64(uint64_t** keys, uint64_t** alt, int64_t count, int lo, int hi,
-                    Alloc& al, cudaStream_t st);
+                    Alloc& al, cudaStream_t st, int* err_dev = nullptr);
 
 }  // namespace tc
 

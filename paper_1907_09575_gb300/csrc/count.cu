@@ -796,25 +796,32 @@ tc_tuning clamp_tuning(const tc_tuning& t) {
     return tt;
 }
 
-UnitLists build_unit_lists(const GraphView* views_dev, const int64_t* vpre_dev, int num, int64_t V,
-                           const tc_tuning& t, Alloc& al, cudaStream_t st) {
+void plan_units(UnitPlan& P, const GraphView* views_dev, const int64_t* vpre_dev, int num, int64_t V,
+                const tc_tuning& t, Alloc& al, cudaStream_t st) {
     const unsigned G = (unsigned)(num_sms() * 8);
-    Buf<int32_t> cs(al, (size_t)std::max<int64_t>(V, 1)), cl(al, (size_t)std::max<int64_t>(V, 1));
-    Buf<int64_t> ps(al, (size_t)(V + 1)), pl(al, (size_t)(V + 1));
+    P.V = V;
+    P.num = num;
+    P.views = views_dev;
+    P.vpre = vpre_dev;
+    P.t = t;
+    P.cs = Buf<int32_t>(al, (size_t)std::max<int64_t>(V, 1));
+    P.cl = Buf<int32_t>(al, (size_t)std::max<int64_t>(V, 1));
+    P.ps = Buf<int64_t>(al, (size_t)(V + 1));
+    P.pl = Buf<int64_t>(al, (size_t)(V + 1));
     if (V > 0) {
         Prof prof_("k_unit_counts", st);
         k_unit_counts<<<grid_for(V, 256, G), 256, 0, st>>>(views_dev, vpre_dev, num, V,
                                                            t.small_max_outdeg, t.warp_unit_tasks,
-                                                           t.cta_unit_tasks, t.slice_max, cs.get(),
-                                                           cl.get());
+                                                           t.cta_unit_tasks, t.slice_max, P.cs.get(),
+                                                           P.cl.get());
     }
     TC_LAUNCH_CHECK();
-    exclusive_scan_i32_to_i64(cs.get(), ps.get(), V, ps.get() + V, al, st);
-    exclusive_scan_i32_to_i64(cl.get(), pl.get(), V, pl.get() + V, al, st);
-    int64_t ns = 0, nl = 0;
-    TC_CUDA(cudaMemcpyAsync(&ns, ps.get() + V, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    TC_CUDA(cudaMemcpyAsync(&nl, pl.get() + V, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    TC_CUDA(cudaStreamSynchronize(st));
+    exclusive_scan_i32_to_i64(P.cs.get(), P.ps.get(), V, P.ps.get() + V, al, st);
+    exclusive_scan_i32_to_i64(P.cl.get(), P.pl.get(), V, P.pl.get() + V, al, st);
+}
+
+UnitLists fill_units(UnitPlan& P, int64_t ns, int64_t nl, Alloc& al, cudaStream_t st) {
+    const unsigned G = (unsigned)(num_sms() * 8);
     UnitLists L;
     L.bytes = sizeof(Unit) * (size_t)std::max<int64_t>(ns + nl, 1);
     L.mem = al.get(L.bytes);
@@ -822,17 +829,44 @@ UnitLists build_unit_lists(const GraphView* views_dev, const int64_t* vpre_dev, 
     L.small = L.large + nl;
     L.nlarge = nl;
     L.nsmall = ns;
-    if (V > 0) {
+    if (P.V > 0) {
         {
             Prof prof_("k_unit_fill", st);
-            k_unit_fill<<<grid_for(V, 256, G), 256, 0, st>>>(views_dev, vpre_dev, num, V,
-                                                             t.small_max_outdeg, t.warp_unit_tasks,
-                                                             t.cta_unit_tasks, t.slice_max, ps.get(),
-                                                             pl.get(), L.small, L.large);
+            k_unit_fill<<<grid_for(P.V, 256, G), 256, 0, st>>>(
+                P.views, P.vpre, P.num, P.V, P.t.small_max_outdeg, P.t.warp_unit_tasks,
+                P.t.cta_unit_tasks, P.t.slice_max, P.ps.get(), P.pl.get(), L.small, L.large);
         }
         TC_LAUNCH_CHECK();
     }
+    P.cs.release();
+    P.cl.release();
+    P.ps.release();
+    P.pl.release();
     return L;
+}
+
+UnitLists build_unit_lists(const GraphView* views_dev, const int64_t* vpre_dev, int num, int64_t V,
+                           const tc_tuning& t, Alloc& al, cudaStream_t st) {
+    UnitPlan P;
+    plan_units(P, views_dev, vpre_dev, num, V, t, al, st);
+    int64_t ns = 0, nl = 0;
+    TC_CUDA(cudaMemcpyAsync(&ns, P.ps.get() + V, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaMemcpyAsync(&nl, P.pl.get() + V, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    return fill_units(P, ns, nl, al, st);
+}
+
+void adopt_units(tc_graph* g, const UnitLists& L, const tc_tuning& tt) {
+    if (g->units_mem) g->alloc.put(g->units_mem, g->units_bytes);
+    g->units_mem = L.mem;
+    g->units_bytes = L.bytes;
+    g->small_units = L.small;
+    g->large_units = L.large;
+    g->n_small = L.nsmall;
+    g->n_large = L.nlarge;
+    g->units_tuning = tt;
+    g->stats.small_units = L.nsmall;
+    g->stats.large_units = L.nlarge;
 }
 
 size_t count_smem_bytes(bool pv, int threads, int unit_tasks) {
@@ -885,20 +919,7 @@ void build_units(tc_graph* g, const tc_tuning& t, cudaStream_t st) {
     const int64_t hv[2] = {0, g->n};
     TC_CUDA(cudaMemcpyAsync(vpre.get(), hv, sizeof(hv), cudaMemcpyHostToDevice, st));
     UnitLists L = build_unit_lists(g->view, vpre.get(), 1, g->n, tt, al, st);
-    TC_CUDA(cudaStreamSynchronize(st));   // hv lives on this stack frame
-    if (g->units_mem) {
-        al.put(g->units_mem, g->units_bytes);
-        g->units_mem = nullptr;
-    }
-    g->units_mem = L.mem;
-    g->units_bytes = L.bytes;
-    g->small_units = L.small;
-    g->large_units = L.large;
-    g->n_small = L.nsmall;
-    g->n_large = L.nlarge;
-    g->units_tuning = tt;
-    g->stats.small_units = L.nsmall;
-    g->stats.large_units = L.nlarge;
+    adopt_units(g, L, tt);
 }
 
 void count_components(const tc_graph* gc, const tc_tuning& t, uint64_t* comp_totals_dev,

@@ -251,9 +251,9 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
     Buf<int64_t> vpre;
     if (num_comps > 0) {
         vpre = Buf<int64_t>(al, (size_t)num_comps + 1);
+        // pageable source: the copy is staged before the call returns
         TC_CUDA(cudaMemcpyAsync(vpre.get(), vpre_host, sizeof(int64_t) * (size_t)(num_comps + 1),
                                 cudaMemcpyHostToDevice, st));
-        TC_CUDA(cudaStreamSynchronize(st));   // vpre_host may go away after the call
     }
     Buf<int64_t> tot(al, 4);  // [0] m, [1] tasks
 
@@ -276,14 +276,10 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
             k_check_comp<<<grid_for(P, kT, G), kT, 0, st>>>(src, dst, P, vpre.get(), num_comps, scal.get());
         }
         TC_LAUNCH_CHECK();
-        int err = 0;
-        TC_CUDA(cudaMemcpyAsync(&err, scal.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
-        TC_CUDA(cudaStreamSynchronize(st));
-        if (err & 1) TC_FAIL(TC_EINVAL, "tc_preprocess: a vertex id lies outside [0, n)");
-        if (err & 2) TC_FAIL(TC_EINVAL, "tc_preprocess_components: a pair joins two components");
         hsrc.release();
         hdst.release();
-        radix_sort_u64(&keys, &alt, P, 0, 2 * bits, al, st);
+        // ids outside [0, n) became sentinels; the error is read at the next sync
+        radix_sort_u64(&keys, &alt, P, 0, 2 * bits, al, st, scal.get());
         {
             Buf<int32_t> fl(al, (size_t)P);
             Buf<int64_t> pos(al, (size_t)P);
@@ -299,10 +295,25 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
                                                                 alt, deg.get());
             }
             TC_LAUNCH_CHECK();
-            TC_CUDA(cudaMemcpyAsync(&m, tot.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-            TC_CUDA(cudaStreamSynchronize(st));
         }
         std::swap(keys, alt);  // E now in `keys`
+    }
+    // one synchronisation for: errors so far, m, max degree
+    int maxdeg = 0;
+    {
+        if (n > 0) {
+            Prof prof_("k_max_i32", st);
+            k_max_i32<<<grid_for(n, kT, G), kT, 0, st>>>(deg.get(), n, scal.get() + 1);
+        }
+        TC_LAUNCH_CHECK();
+        int hs[2] = {0, 0};
+        TC_CUDA(cudaMemcpyAsync(hs, scal.get(), 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (P > 0) TC_CUDA(cudaMemcpyAsync(&m, tot.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaStreamSynchronize(st));
+        if (hs[0] & 1) TC_FAIL(TC_EINVAL, "tc_preprocess: a vertex id lies outside [0, n)");
+        if (hs[0] & 2) TC_FAIL(TC_EINVAL, "tc_preprocess_components: a pair joins two components");
+        if (hs[0] & 4) TC_FAIL(TC_ETIMEOUT, "tc_preprocess: a sort look-back wait ran past its bound");
+        maxdeg = hs[1];
     }
     g->m = m;
     g->stats.m = m;
@@ -344,16 +355,8 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
         g->num_comps = num_comps;
     }
 
-    // a3 max degree, a4 relabel
-    int maxdeg = 0;
+    // a4 relabel
     if (n > 0) {
-        {
-            Prof prof_("k_max_i32", st);
-            k_max_i32<<<grid_for(n, kT, G), kT, 0, st>>>(deg.get(), n, scal.get() + 1);
-        }
-        TC_LAUNCH_CHECK();
-        TC_CUDA(cudaMemcpyAsync(&maxdeg, scal.get() + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-        TC_CUDA(cudaStreamSynchronize(st));
         Buf<uint64_t> dk(al, (size_t)n), da(al, (size_t)n);
         uint64_t* dkeys = dk.get();
         uint64_t* dalt = da.get();
@@ -363,7 +366,7 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
         }
         TC_LAUNCH_CHECK();
         int dbits = ceil_log2_u64((uint64_t)maxdeg + 1);
-        radix_sort_u64(&dkeys, &dalt, n, bits, bits + dbits, al, st);
+        radix_sort_u64(&dkeys, &dalt, n, bits, bits + dbits, al, st, scal.get());
         {
             Prof prof_("k_perm", st);
             k_perm<<<grid_for(n, kT, G), kT, 0, st>>>(dkeys, n, bits, g->perm);
@@ -389,7 +392,7 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
         }
         TC_LAUNCH_CHECK();
         std::swap(keys, alt);
-        radix_sort_u64(&keys, &alt, m, 0, 2 * bits, al, st);
+        radix_sort_u64(&keys, &alt, m, 0, 2 * bits, al, st, scal.get());
         {
             Prof prof_("k_adj_rows", st);
             k_adj_rows<<<grid_for(m, kT, G), kT, 0, st>>>(keys, m, bits, g->adj, dplus.get());
@@ -461,19 +464,7 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
             }
         TC_LAUNCH_CHECK();
     }
-    unsigned long long hprobes = 0;
-    int64_t ntasks = 0;
-    TC_CUDA(cudaMemcpyAsync(&maxout, scal.get() + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
-    TC_CUDA(cudaMemcpyAsync(&hprobes, probes.get(), sizeof(hprobes), cudaMemcpyDeviceToHost, st));
-    TC_CUDA(cudaMemcpyAsync(&ntasks, g->loff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    TC_CUDA(cudaStreamSynchronize(st));
-    g->n_tasks = ntasks;
-    g->stats.max_outdeg = maxout;
-    g->stats.tasks = ntasks;
-    g->stats.probes = hprobes;
-    g->stats.offset_bytes = (int32_t)ob;
-
-    // the device view the count kernel reads
+    // the device view the count kernel reads (pageable sources: staged on return)
     {
         GraphView v{};
         v.off = g->off;
@@ -490,13 +481,36 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
         vc.comp = g->comp;
         vc.comp_totals = g->comp_totals;
         TC_CUDA(cudaMemcpyAsync(g->view_comp, &vc, sizeof(vc), cudaMemcpyHostToDevice, st));
-        TC_CUDA(cudaStreamSynchronize(st));
     }
 
-    // work units for the default tuning
+    // a6 work units for the default tuning, sized at the same synchronisation
+    // as the task statistics
     tc_tuning def;
     tuning_defaults(&def);
-    build_units(g, def, st);
+    def = clamp_tuning(def);
+    Buf<int64_t> gvpre(al, 2);
+    const int64_t hv[2] = {0, n};
+    TC_CUDA(cudaMemcpyAsync(gvpre.get(), hv, sizeof(hv), cudaMemcpyHostToDevice, st));
+    UnitPlan plan;
+    plan_units(plan, g->view, gvpre.get(), 1, n, def, al, st);
+    unsigned long long hprobes = 0;
+    int64_t ntasks = 0, ns = 0, nl = 0;
+    int herr = 0;
+    TC_CUDA(cudaMemcpyAsync(&maxout, scal.get() + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaMemcpyAsync(&herr, scal.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaMemcpyAsync(&hprobes, probes.get(), sizeof(hprobes), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaMemcpyAsync(&ntasks, g->loff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaMemcpyAsync(&ns, plan.ps.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaMemcpyAsync(&nl, plan.pl.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    if (herr & 4) TC_FAIL(TC_ETIMEOUT, "tc_preprocess: a sort look-back wait ran past its bound");
+    g->n_tasks = ntasks;
+    g->stats.max_outdeg = maxout;
+    g->stats.tasks = ntasks;
+    g->stats.probes = hprobes;
+    g->stats.offset_bytes = (int32_t)ob;
+    UnitLists L = fill_units(plan, ns, nl, al, st);
+    adopt_units(g, L, def);
     g->stats.device_bytes = (int64_t)(g->arena_bytes + g->units_bytes);
 }
 

@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint64_t* __rest
 }  // namespace
 
 void radix_sort_u64(uint64_t** keys, uint64_t** alt, int64_t count, int lo, int hi, Alloc& al,
-                    cudaStream_t st) {
+                    cudaStream_t st, int* err_dev) {
     if (count <= 1 || hi <= lo) return;
     const int64_t ntiles = (count + kTile - 1) / kTile;
     const int npass = (hi - lo + 7) / 8;
@@ -242,7 +242,7 @@ void radix_sort_u64(uint64_t** keys, uint64_t** alt, int64_t count, int lo, int 
     Buf<unsigned long long> hist(al, (size_t)kMaxPasses * kRadix + 8);
     Buf<unsigned long long> status(al, (size_t)ntiles * kRadix);
     unsigned* ctrs = reinterpret_cast<unsigned*>(hist.get() + (size_t)kMaxPasses * kRadix);
-    int* err = reinterpret_cast<int*>(ctrs + kMaxPasses);
+    int* err = err_dev ? err_dev : reinterpret_cast<int*>(ctrs + kMaxPasses);
     TC_CUDA(cudaMemsetAsync(hist.get(), 0, sizeof(unsigned long long) * ((size_t)kMaxPasses * kRadix + 8), st));
     {
         Prof prof_("k_digit_hist", st);
@@ -270,6 +270,7 @@ void radix_sort_u64(uint64_t** keys, uint64_t** alt, int64_t count, int lo, int 
         *keys = *alt;
         *alt = t;
     }
+    if (err_dev) return;   // the caller reads the flag at its next synchronisation
     int herr = 0;
     TC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     TC_CUDA(cudaStreamSynchronize(st));

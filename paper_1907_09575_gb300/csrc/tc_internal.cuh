@@ -42,6 +42,23 @@ struct UnitLists {
     int64_t nlarge = 0, nsmall = 0;
 };
 
+// Unit building in two phases: plan_units launches the counting kernels and
+// scans (the list sizes land at ps[V], pl[V] on the device); once the host
+// knows them, fill_units allocates and fills the lists.
+struct UnitPlan {
+    Buf<int32_t> cs, cl;
+    Buf<int64_t> ps, pl;
+    int64_t V = 0;
+    int num = 0;
+    const GraphView* views = nullptr;
+    const int64_t* vpre = nullptr;
+    tc_tuning t{};
+};
+void plan_units(UnitPlan& P, const GraphView* views_dev, const int64_t* vpre_dev, int num, int64_t V,
+                const tc_tuning& t, Alloc& al, cudaStream_t st);
+UnitLists fill_units(UnitPlan& P, int64_t ns, int64_t nl, Alloc& al, cudaStream_t st);
+void adopt_units(tc_graph* g, const UnitLists& L, const tc_tuning& tt);
+
 tc_tuning clamp_tuning(const tc_tuning& t);
 UnitLists build_unit_lists(const GraphView* views_dev, const int64_t* vpre_dev, int num, int64_t V,
                            const tc_tuning& t, Alloc& al, cudaStream_t st);
