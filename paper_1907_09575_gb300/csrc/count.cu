@@ -119,6 +119,10 @@ struct BitTab {
         if (!PV) return 0;
         return (int)pre[d >> 5] + __popc(w & ((1u << (d & 31)) - 1u));
     }
+    // hit counters by rank (rank < slice <= 4096): one word each, so hits on
+    // neighbouring entries never share an atomic's word
+    __device__ __forceinline__ void credit(unsigned* cnt, int r) const { atomicAdd(&cnt[r], 1u); }
+    __device__ __forceinline__ unsigned credited(const unsigned* cnt, int r) const { return cnt[r]; }
 };
 
 struct HashTab {
@@ -139,6 +143,15 @@ struct HashTab {
             b = (b + 1) & bmask;
         }
     }
+    // hit counters by slot (up to twice the slice): 16 bits each, two a
+    // word (a counter never exceeds the tasks of a unit, below 2^16 by the
+    // unit size cap)
+    __device__ __forceinline__ void credit(unsigned* cnt, int r) const {
+        atomicAdd(&cnt[r >> 1], 1u << ((r & 1) << 4));
+    }
+    __device__ __forceinline__ unsigned credited(const unsigned* cnt, int r) const {
+        return (cnt[r >> 1] >> ((r & 1) << 4)) & 0xffffu;
+    }
 };
 
 __device__ __forceinline__ void hash_insert(int* tab, unsigned bmask, int k) {
@@ -157,14 +170,6 @@ __device__ __forceinline__ unsigned hash_buckets(int dp) {
     return b;
 }
 
-// 16-bit hit counters, two per word (a counter never exceeds the tasks of a
-// unit, kept below 2^16 by the unit size cap).
-__device__ __forceinline__ void count_hit(unsigned* cnt, int r) {
-    atomicAdd(&cnt[r >> 1], 1u << ((r & 1) << 4));
-}
-__device__ __forceinline__ unsigned hit_count(const unsigned* cnt, int r) {
-    return (cnt[r >> 1] >> ((r & 1) << 4)) & 0xffffu;
-}
 
 // ---------------------------------------------------------------------------
 // One warp walks one long tail (>= 32 entries) adj[st, st+L).  The 16-byte
@@ -179,7 +184,7 @@ __device__ __forceinline__ void probe_one(const Tab& T, int k, unsigned* cnt, un
     const int r = T.template find<PV>(k);
     if (r >= 0) {
         ++mine;
-        if (PV) count_hit(cnt, r);
+        if (PV) T.credit(cnt, r);
     }
 }
 
@@ -216,9 +221,7 @@ __device__ __forceinline__ unsigned warp_walk_tail_vec(int64_t st, int L, const 
     }
     hits += mine;
     if (!PV) return 0;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
-    return mine;
+    return __reduce_add_sync(0xffffffffu, mine);
 }
 
 template <bool PV, class Tab>
@@ -251,9 +254,7 @@ __device__ __forceinline__ unsigned warp_walk_tail_scalar(int64_t st, int L, con
     }
     hits += mine;
     if (!PV) return 0;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
-    return mine;
+    return __reduce_add_sync(0xffffffffu, mine);
 }
 
 template <bool PV, class Tab>
@@ -277,8 +278,10 @@ __device__ __forceinline__ unsigned warp_walk_tail(int64_t st, int L, const int3
 // starting inside the step before q (a ballot and a warp OR-reduce), minus
 // one; the short tasks' start - prefix are compacted into s_base by rank, so
 // the address is s_base[owner] + q.
-// PV: a short task's hits are the popcounts of the hit ballots over its span;
-// each task's hits go once to tnew[i]; per-entry hits to the counters cnt.
+// PV: lane s keeps the hit ballot of step s (a group's short tails total at
+// most 31 * 32 entries, so 31 steps); a short task, which spans at most two
+// steps, takes its hits from their popcounts over its positions at the end.
+// Each task's hits go once to tnew[i]; per-entry hits to the counters cnt.
 // ---------------------------------------------------------------------------
 template <bool PV, class Tab>
 __device__ __forceinline__ void warp_probe_group(const Task* __restrict__ tasks, int64_t tb, int64_t t1,
@@ -332,6 +335,7 @@ __device__ __forceinline__ void warp_probe_group(const Task* __restrict__ tasks,
     if (sv) s_base[__popc(shortm & (le >> 1))] = start - excl;
     __syncwarp();
     probes += (uint64_t)total;
+    unsigned step_hits = 0;   // PV: the hit ballot of step `lane`
     for (int q0 = 0; q0 < total; q0 += 32 * kUnroll) {
         int k[kUnroll];
 #pragma unroll
@@ -354,11 +358,18 @@ __device__ __forceinline__ void warp_probe_group(const Task* __restrict__ tasks,
             hits += hit ? 1 : 0;
             if (PV) {
                 const unsigned hm = __ballot_sync(0xffffffffu, hit);
-                const int qb = q0 + 32 * u;
-                const int plo = max(excl - qb, 0), phi = min(excl + slen - qb, 32);
-                if (sv && plo < phi) c += __popc(hm & bit_range(plo, phi));
-                if (hit) count_hit(cnt, r[u]);
+                if (lane == (q0 >> 5) + u) step_hits = hm;
+                if (hit) T.credit(cnt, r[u]);
             }
+        }
+    }
+    if (PV && total > 0) {
+        const int s0 = excl >> 5, b0 = excl & 31;
+        const unsigned h0 = __shfl_sync(0xffffffffu, step_hits, s0);
+        const unsigned h1 = __shfl_sync(0xffffffffu, step_hits, (s0 + 1) & 31);
+        if (sv) {
+            c += __popc(h0 & bit_range(b0, min(b0 + slen, 32)));
+            if (b0 + slen > 32) c += __popc(h1 & bit_range(0, b0 + slen - 32));
         }
     }
     __syncwarp();   // s_base is rewritten by the warp's next group
@@ -444,11 +455,11 @@ __device__ __forceinline__ void warp_unit(const GraphView& G, const Unit& U, uns
         __syncwarp();
         if (PV) {
             if (lane < dp) {
-                const unsigned h = hit_count(cnt, lane);
+                const unsigned h = T.credited(cnt, lane);
                 if (h) atomicAdd(&G.tnew[mine], (unsigned long long)h);
             }
             if (lane + 32 < dp) {
-                const unsigned h = hit_count(cnt, lane + 32);
+                const unsigned h = T.credited(cnt, lane + 32);
                 if (h) atomicAdd(&G.tnew[mine2], (unsigned long long)h);
             }
         }
@@ -467,7 +478,7 @@ __device__ __forceinline__ void warp_unit(const GraphView& G, const Unit& U, uns
         __syncwarp();
         if (PV)
             for (int s = lane; s < kSmallTable; s += 32) {
-                const unsigned h = hit_count(cnt, s);
+                const unsigned h = T.credited(cnt, s);
                 if (h) atomicAdd(&G.tnew[tab[s]], (unsigned long long)h);
             }
     }
@@ -584,7 +595,7 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
         __syncthreads();
         if (PV)
             for (int r = threadIdx.x; r < dp; r += blockDim.x) {
-                const unsigned h = hit_count(cnt, r);
+                const unsigned h = T.credited(cnt, r);
                 if (h) atomicAdd(&G.tnew[G.adj[rb + r]], (unsigned long long)h);
             }
     } else {
@@ -600,7 +611,7 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
         __syncthreads();
         if (PV)
             for (int s = threadIdx.x; s < 4 * (int)buckets; s += blockDim.x) {
-                const unsigned h = hit_count(cnt, s);
+                const unsigned h = T.credited(cnt, s);
                 if (h) atomicAdd(&G.tnew[tab[s]], (unsigned long long)h);
             }
     }

@@ -47,11 +47,20 @@ __global__ void k_unique_flags(const uint64_t* __restrict__ keys, int64_t P, uin
 }
 
 // Adds c to counter[v] once per group of lanes holding the same v.
-__device__ __forceinline__ void warp_add(int32_t* counter, int32_t v, bool active, int c = 1) {
-    unsigned act = __ballot_sync(0xffffffffu, active);
-    if (!active) return;
-    unsigned peers = __match_any_sync(act, v);
-    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&counter[v], c * __popc(peers));
+// counter[v] += 1 for the active lanes, whose v are non-decreasing across the
+// warp: one atomic per run of equal v among neighbouring active lanes (an
+// inactive lane splits a run; both parts are added).  All 32 lanes call it.
+__device__ __forceinline__ void warp_add_sorted(int32_t* counter, int32_t v, bool active) {
+    const int lane = threadIdx.x & 31;
+    const int32_t pv = __shfl_up_sync(0xffffffffu, v, 1);
+    const bool pa = __shfl_up_sync(0xffffffffu, active, 1);
+    const bool cont = active && lane > 0 && pa && pv == v;
+    const unsigned C = __ballot_sync(0xffffffffu, cont);   // lanes continuing a run
+    if (active && !cont) {
+        // run length: 1 + the continuation lanes right after this one
+        const unsigned rest = lane == 31 ? 0u : (C >> (lane + 1));
+        atomicAdd(&counter[v], 1 + __ffs(~rest) - 1);
+    }
 }
 
 __global__ void k_unique_compact(const uint64_t* __restrict__ keys, const int32_t* __restrict__ flags,
@@ -65,8 +74,8 @@ __global__ void k_unique_compact(const uint64_t* __restrict__ keys, const int32_
         bool keep = e < P && flags[e];
         uint64_t k = keep ? keys[e] : 0;
         if (keep) E[pos[e]] = k;
-        warp_add(deg, (int32_t)(k >> bits), keep);
-        warp_add(deg, (int32_t)(k & mask), keep);
+        warp_add_sorted(deg, (int32_t)(k >> bits), keep);   // keys sorted: min ids in runs
+        if (keep) atomicAdd(&deg[(int32_t)(k & mask)], 1);
     }
 }
 
@@ -117,7 +126,7 @@ __global__ void k_adj_rows(const uint64_t* __restrict__ keys, int64_t m, int bit
         bool ok = e < m;
         uint64_t k = ok ? keys[e] : 0;
         if (ok) adj[e] = (int32_t)(k & mask);
-        warp_add(dplus, (int32_t)(k >> bits), ok);
+        warp_add_sorted(dplus, (int32_t)(k >> bits), ok);
     }
 }
 
@@ -156,26 +165,43 @@ __global__ void k_task_count(const uint64_t* __restrict__ keys, int64_t m, int b
     if ((threadIdx.x & 31) == 0 && my) atomicAdd(probes, my);
 }
 
-// fill[j] starts at the first task slot of pivot j and is advanced atomically.
+// fill[j] starts at the first task slot of pivot j and is advanced
+// atomically; each thread keeps kFillILP edges' atomics in flight at once.
+constexpr int kFillILP = 4;
+
 template <class OffT>
 __global__ void k_task_fill(const uint64_t* __restrict__ keys, int64_t m, int bits,
                             const OffT* __restrict__ off, unsigned long long* __restrict__ fill,
                             Task* __restrict__ tasks) {
     const uint64_t mask = (1ull << bits) - 1ull;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t k = keys[e];
-        const int64_t i = (int64_t)(k >> bits);
-        const int32_t j = (int32_t)(k & mask);
-        const int64_t len = (int64_t)off[i + 1] - e - 1;
-        if (len > 0) {
-            const unsigned long long slot = atomicAdd(&fill[j], 1ull);
-            Task t;
-            t.start = e + 1;
-            t.len = (int32_t)len;
-            t.i = (int32_t)i;
-            tasks[slot] = t;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e0 < m; e0 += stride * kFillILP) {
+        int64_t i[kFillILP], len[kFillILP];
+        int32_t j[kFillILP];
+#pragma unroll
+        for (int u = 0; u < kFillILP; ++u) {
+            const int64_t e = e0 + u * stride;
+            len[u] = 0;
+            if (e < m) {
+                const uint64_t k = keys[e];
+                i[u] = (int64_t)(k >> bits);
+                j[u] = (int32_t)(k & mask);
+                len[u] = (int64_t)off[i[u] + 1] - e - 1;
+            }
         }
+        unsigned long long slot[kFillILP];
+#pragma unroll
+        for (int u = 0; u < kFillILP; ++u)
+            if (len[u] > 0) slot[u] = atomicAdd(&fill[j[u]], 1ull);
+#pragma unroll
+        for (int u = 0; u < kFillILP; ++u)
+            if (len[u] > 0) {
+                Task t;
+                t.start = e0 + u * stride + 1;
+                t.len = (int32_t)len[u];
+                t.i = (int32_t)i[u];
+                tasks[slot[u]] = t;
+            }
     }
 }
 
