@@ -29,24 +29,10 @@
 namespace tc {
 namespace {
 
-#ifndef TC_VEC_WALK
-#define TC_VEC_WALK 0          // long tails read as int4 (1) or as int (0)
-#endif
-#ifndef TC_PREFETCH
-#define TC_PREFETCH 1          // prefetch the next long task's record and tail head
-#endif
-#ifndef TC_FULLSTEP
-#define TC_FULLSTEP 1          // unchecked full steps in the long-tail walk
-#endif
-#ifndef TC_DEFER_CREDIT
-#define TC_DEFER_CREDIT 0      // all lookups of an unrolled step before its per-entry credits
-#endif
 #ifndef TC_LARGE_MINB
 #define TC_LARGE_MINB 4        // CTAs per SM the CTA kernel's registers must allow
 #endif
 
-constexpr int kSmallWarps = 8;
-constexpr int kSmallThreads = kSmallWarps * 32;
 constexpr int kGrab = 4;          // warp units popped per queue access
 constexpr int kEmpty = -1;
 #ifndef TC_UNROLL
@@ -171,14 +157,6 @@ __device__ __forceinline__ unsigned hash_buckets(int dp) {
 }
 
 
-// ---------------------------------------------------------------------------
-// One warp walks one long tail (>= 32 entries) adj[st, st+L).  The 16-byte
-// aligned body is read as int4 (lane p takes entries 4p..4p+3 of a 128-entry
-// step, two steps in flight); the unaligned head and the last < 4 entries
-// (at most 6) go to lanes 0..5.  Returns the task's hits (same in all lanes).
-// ---------------------------------------------------------------------------
-constexpr int kVecUnroll = 2;
-
 template <bool PV, class Tab>
 __device__ __forceinline__ void probe_one(const Tab& T, int k, unsigned* cnt, unsigned& mine) {
     const int r = T.template find<PV>(k);
@@ -188,83 +166,62 @@ __device__ __forceinline__ void probe_one(const Tab& T, int k, unsigned* cnt, un
     }
 }
 
-template <bool PV, class Tab>
-__device__ __forceinline__ unsigned warp_walk_tail_vec(int64_t st, int L, const int32_t* __restrict__ adj,
-                                                   const Tab& T, unsigned* cnt, uint64_t& hits) {
-    const int lane = threadIdx.x & 31;
-    const int h = min((int)((4 - (st & 3)) & 3), L);        // entries before the first 16-B boundary
-    const int nchunks = (L - h) >> 2;
-    const int rest = L - h - 4 * nchunks;                    // entries after the last full chunk
-    unsigned mine = 0;
-    // head and rest: at most 3 + 3 entries
-    if (lane < h + rest) {
-        const int q = (lane < h) ? lane : (h + 4 * nchunks + (lane - h));
-        probe_one<PV>(T, __ldg(&adj[st + q]), cnt, mine);
-    }
-    const int4* body = reinterpret_cast<const int4*>(adj + st + h);
-    for (int c0 = 0; c0 < nchunks; c0 += 32 * kVecUnroll) {
-        int4 v[kVecUnroll];
-#pragma unroll
-        for (int u = 0; u < kVecUnroll; ++u) {
-            const int c = c0 + 32 * u + lane;
-            v[u] = (c < nchunks) ? __ldg(&body[c]) : make_int4(-1, -1, -1, -1);
-        }
-#pragma unroll
-        for (int u = 0; u < kVecUnroll; ++u) {
-            if (v[u].x >= 0) {
-                probe_one<PV>(T, v[u].x, cnt, mine);
-                probe_one<PV>(T, v[u].y, cnt, mine);
-                probe_one<PV>(T, v[u].z, cnt, mine);
-                probe_one<PV>(T, v[u].w, cnt, mine);
-            }
-        }
-    }
-    hits += mine;
-    if (!PV) return 0;
-    return __reduce_add_sync(0xffffffffu, mine);
-}
-
-template <bool PV, class Tab>
-__device__ __forceinline__ unsigned warp_walk_tail_scalar(int64_t st, int L, const int32_t* __restrict__ adj,
-                                                          const Tab& T, unsigned* cnt, uint64_t& hits) {
-    const int lane = threadIdx.x & 31;
-    const int32_t* __restrict__ p = adj + st + lane;
-    unsigned mine = 0;
-    int q0 = 0;
-#if TC_FULLSTEP
-    // full steps: every lane reads kUnroll entries, no bounds checks
-    for (; q0 + 32 * kUnroll <= L; q0 += 32 * kUnroll) {
-        int k[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) k[u] = __ldg(p + q0 + 32 * u);
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) probe_one<PV>(T, k[u], cnt, mine);
-    }
-#endif
-    for (; q0 < L; q0 += 32 * kUnroll) {
-        int k[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int q = q0 + 32 * u + lane;
-            k[u] = (q < L) ? __ldg(p + q0 + 32 * u) : -1;
-        }
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-            if (k[u] >= 0) probe_one<PV>(T, k[u], cnt, mine);
-    }
-    hits += mine;
-    if (!PV) return 0;
-    return __reduce_add_sync(0xffffffffu, mine);
-}
-
+// ---------------------------------------------------------------------------
+// One warp walks one long tail (>= 32 entries) adj[st, st+L): lane q of a
+// step reads entry q, kUnroll steps a round.  Returns the task's hits (the
+// same in all lanes) with per-vertex counts, else 0.
+//
+// Per-vertex: the next round's entries are loaded before this round is
+// probed, so a tail of up to 2 * 32 * kUnroll entries waits on memory about
+// once.  Totals only: unchecked full rounds, then a checked last one -- the
+// lighter probe leaves no latency worth the extra registers to hide.
+// ---------------------------------------------------------------------------
 template <bool PV, class Tab>
 __device__ __forceinline__ unsigned warp_walk_tail(int64_t st, int L, const int32_t* __restrict__ adj,
                                                    const Tab& T, unsigned* cnt, uint64_t& hits) {
-#if TC_VEC_WALK
-    return warp_walk_tail_vec<PV>(st, L, adj, T, cnt, hits);
-#else
-    return warp_walk_tail_scalar<PV>(st, L, adj, T, cnt, hits);
-#endif
+    const int lane = threadIdx.x & 31;
+    const int32_t* __restrict__ p = adj + st + lane;
+    unsigned mine = 0;
+    if constexpr (PV) {
+        int k[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) k[u] = (32 * u + lane < L) ? __ldg(p + 32 * u) : -1;
+        for (int q0 = 0; q0 < L; q0 += 32 * kUnroll) {
+            const int q1 = q0 + 32 * kUnroll;
+            int kn[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) kn[u] = (q1 + 32 * u + lane < L) ? __ldg(p + q1 + 32 * u) : -1;
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                if (k[u] >= 0) probe_one<PV>(T, k[u], cnt, mine);
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) k[u] = kn[u];
+        }
+        hits += mine;
+        return __reduce_add_sync(0xffffffffu, mine);
+    } else {
+        int q0 = 0;
+        for (; q0 + 32 * kUnroll <= L; q0 += 32 * kUnroll) {
+            int k[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) k[u] = __ldg(p + q0 + 32 * u);
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) probe_one<PV>(T, k[u], cnt, mine);
+        }
+        if (q0 < L) {
+            int k[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int q = q0 + 32 * u + lane;
+                k[u] = (q < L) ? __ldg(p + q0 + 32 * u) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                if (k[u] >= 0) probe_one<PV>(T, k[u], cnt, mine);
+        }
+        hits += mine;
+        return 0;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -495,8 +452,8 @@ __device__ __forceinline__ void warp_unit(const GraphView& G, const Unit& U, uns
 // CTA unit: a slice of a larger pivot with its table shared by the CTA.
 // Phase A: warps take groups of 32 tasks from a shared counter, probe the
 // short tails and queue the long ones; phase B: warps pop one long task at a
-// time, the next task's record loaded (and its tail head prefetched) before
-// the current tail is walked.
+// time, with later tasks' records already loading and the next tail
+// prefetched into L2 while the current tail is walked.
 // ---------------------------------------------------------------------------
 template <bool PV, class Tab>
 __device__ __forceinline__ void cta_probe_unit(const GraphView& G, const Unit& U, const Tab& T,
@@ -518,30 +475,59 @@ __device__ __forceinline__ void cta_probe_unit(const GraphView& G, const Unit& U
     }
     __syncthreads();
     const int nlong = s_ctl[1];
-    int x = 0;
-    if (lane == 0) x = atomicAdd(&s_ctl[2], 1);
-    x = __shfl_sync(0xffffffffu, x, 0);
-    Task cur;
-    cur.len = 0;
-    if (x < nlong) cur = tasks[U.t0 + s_long[x]];
-    while (x < nlong) {
-        int xn = 0;
-        if (lane == 0) xn = atomicAdd(&s_ctl[2], 1);
-        xn = __shfl_sync(0xffffffffu, xn, 0);
-        Task nxt;
-        nxt.len = 0;
-        if (xn < nlong) {
-            nxt = tasks[U.t0 + s_long[xn]];
-#if TC_PREFETCH
-            if (32 * lane < nxt.len)
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(adj + nxt.start + 32 * lane));
-#endif
+    auto pop = [&]() {
+        int v = 0;
+        if (lane == 0) v = atomicAdd(&s_ctl[2], 1);
+        return __shfl_sync(0xffffffffu, v, 0);
+    };
+    auto record = [&](int x) {
+        Task t;
+        t.len = 0;
+        if (x < nlong) t = tasks[U.t0 + s_long[x]];
+        return t;
+    };
+    // the next task's tail is prefetched into L2 while this one is walked
+    auto prefetch_tail = [&](const Task& t) {
+        if (32 * lane < t.len) asm volatile("prefetch.global.L2 [%0];" ::"l"(adj + t.start + 32 * lane));
+    };
+    if constexpr (!PV) {
+        // records two tasks ahead: the record load of task x+2 overlaps the
+        // walk of task x, and the prefetch of x+1's tail waits on nothing
+        int x = pop(), x1 = pop();
+        Task cur = record(x), nxt = record(x1);
+        while (x < nlong) {
+            const int x2 = pop();
+            const Task nn = record(x2);
+            prefetch_tail(nxt);
+            probes += (uint64_t)cur.len;
+            warp_walk_tail<PV>(cur.start, cur.len, adj, T, cnt, uh);
+            x = x1;
+            x1 = x2;
+            cur = nxt;
+            nxt = nn;
         }
-        probes += (uint64_t)cur.len;
-        const unsigned ch = warp_walk_tail<PV>(cur.start, cur.len, adj, T, cnt, uh);
-        if (PV && lane == 0 && ch) atomicAdd(&G.tnew[cur.i], (unsigned long long)ch);
-        x = xn;
-        cur = nxt;
+    } else {
+        // one task ahead (a third record would spill the per-vertex kernel;
+        // written out, as the helpers above cost it registers too)
+        int x = pop();
+        Task cur;
+        cur.len = 0;
+        if (x < nlong) cur = tasks[U.t0 + s_long[x]];
+        while (x < nlong) {
+            const int xn = pop();
+            Task nxt;
+            nxt.len = 0;
+            if (xn < nlong) {
+                nxt = tasks[U.t0 + s_long[xn]];
+                if (32 * lane < nxt.len)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(adj + nxt.start + 32 * lane));
+            }
+            probes += (uint64_t)cur.len;
+            const unsigned ch = warp_walk_tail<PV>(cur.start, cur.len, adj, T, cnt, uh);
+            if (lane == 0 && ch) atomicAdd(&G.tnew[cur.i], (unsigned long long)ch);
+            x = xn;
+            cur = nxt;
+        }
     }
 }
 
