@@ -56,9 +56,11 @@ typedef enum {
  * <j,i,k> task lists, the work units and the relabelling. */
 typedef struct tc_graph tc_graph;
 
-/* Caller-supplied device allocator; NULL selects cudaMallocAsync on the
- * call's stream.  alloc returns NULL on failure.  free receives the size
- * that was allocated. */
+/* Caller-supplied device allocator; NULL selects the library's own
+ * stream-ordered memory pool on the current device, allocated and freed on
+ * the call's stream.  That pool keeps freed memory reserved for later calls
+ * (tc_release_memory returns it).  alloc returns NULL on failure.  free
+ * receives the size that was allocated. */
 typedef struct {
     void* (*alloc)(size_t bytes, void* ctx, void* stream);
     void (*free)(void* ptr, size_t bytes, void* ctx, void* stream);
@@ -112,7 +114,7 @@ typedef struct {
  *              ownership and may free them once the call returns.
  *   num_pairs  >= 0.          n  number of vertices, 0 <= n < 2^31.
  *   flags      TC_INPUT_ON_DEVICE, TC_OFFSETS_32, TC_OFFSETS_64.
- *   alloc      device allocator, or NULL for cudaMallocAsync.
+ *   alloc      device allocator, or NULL for the library's pool.
  *   stream     cudaStream_t as void*.  The call synchronises it.
  *   out        receives the new graph (owned by the caller until
  *              tc_graph_free); untouched on failure.
@@ -207,6 +209,15 @@ TC_API tc_status tc_graph_get_stats(const tc_graph* g, tc_graph_stats* out);
 /* Releases the graph's arena on the stream given at preprocessing.
  * NULL is accepted and ignored. */
 TC_API void tc_graph_free(tc_graph* g);
+
+/* Returns to the device the memory that the library's pool of `device`
+ * holds but no graph, batch or server uses (device < 0: every device).  The
+ * pool keeps freed memory so that repeated calls reuse it rather than map it
+ * again; a caller that needs the memory elsewhere calls this after the
+ * streams that freed library memory have completed.  Not part of the paper's
+ * method.  TC_EINVAL for a device index above the library's limit (64);
+ * TC_ECUDA. */
+TC_API tc_status tc_release_memory(int device);
 
 /* Defaults for every tc_tuning field.  TC_EINVAL on NULL. */
 TC_API tc_status tc_tuning_default(tc_tuning* out);

@@ -1,6 +1,7 @@
 // C ABI entry points: argument checks, error capture, allocation, ownership.
 #include <cstdarg>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "common.cuh"
@@ -19,6 +20,34 @@ void set_error(const char* fmt, ...) {
 
 void clear_error() { g_err[0] = 0; }
 
+// The library's stream-ordered memory pool of each device.  Freed blocks stay
+// reserved for the next call (no release threshold): a graph's arena and its
+// preprocessing scratch are tens of GB at the larger workloads, and mapping
+// them afresh on every call costs more than the kernels of a small step.
+// tc_release_memory hands the unused part back.
+constexpr int kMaxDevices = 64;
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[kMaxDevices] = {};
+
+static cudaMemPool_t library_pool(int dev) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (dev < 0 || dev >= kMaxDevices) TC_FAIL(TC_EINVAL, "device %d out of range", dev);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        TC_CUDA(cudaMemPoolCreate(&pool, &props));
+        uint64_t keep = ~0ull;
+        TC_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        g_pool[dev] = pool;
+    }
+    return g_pool[dev];
+}
+
 void* Alloc::get(size_t bytes) {
     void* p = nullptr;
     if (has_user) {
@@ -26,12 +55,23 @@ void* Alloc::get(size_t bytes) {
         if (!p) TC_FAIL(TC_ENOMEM, "device allocation of %zu bytes failed (caller allocator)", bytes);
         return p;
     }
-    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    int dev = 0;
+    TC_CUDA(cudaGetDevice(&dev));
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, library_pool(dev), stream);
     if (e != cudaSuccess || !p) {
         cudaGetLastError();
-        TC_FAIL(TC_ENOMEM, "cudaMallocAsync of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        TC_FAIL(TC_ENOMEM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
     }
     return p;
+}
+
+void release_pool(int dev) {
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (dev >= 0 && dev < kMaxDevices) pool = g_pool[dev];
+    }
+    if (pool) TC_CUDA(cudaMemPoolTrimTo(pool, 0));
 }
 
 void Alloc::put(void* p, size_t bytes) {
@@ -285,5 +325,16 @@ tc_status tc_count_get_stats(const tc_graph* g, tc_count_stats* out, void* strea
 }
 
 void tc_graph_free(tc_graph* g) { graph_release(g); }
+
+tc_status tc_release_memory(int device) {
+    TC_API_BEGIN
+    if (device >= kMaxDevices) TC_FAIL(TC_EINVAL, "tc_release_memory: device %d out of range", device);
+    if (device >= 0) {
+        release_pool(device);
+    } else {
+        for (int d = 0; d < kMaxDevices; ++d) release_pool(d);
+    }
+    TC_API_END
+}
 
 }  // extern "C"

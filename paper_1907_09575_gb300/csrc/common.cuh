@@ -54,7 +54,7 @@ private:
 };
 
 // ---------------------------------------------------------------------------
-// device memory through the caller's allocator (or cudaMallocAsync)
+// device memory through the caller's allocator (or the library's pool)
 // ---------------------------------------------------------------------------
 struct Alloc {
     tc_allocator user{};

@@ -39,7 +39,8 @@ constexpr int kEmpty = -1;
 #define TC_UNROLL 4
 #endif
 constexpr int kUnroll = TC_UNROLL;   // independent loads in flight per lane
-// warp unit table region: 128 hash slots, or a 128-word bitmap (4096 labels)
+// warp unit table region: 128 hash slots, or a 128-word bitmap (4095 labels
+// and the guard bit)
 // plus its 128 16-bit rank prefixes
 constexpr int kSmallBitWords = 128;
 constexpr int kSmallRegionWords = kSmallBitWords + kSmallBitWords / 2;
@@ -96,14 +97,22 @@ struct BitTab {
     const unsigned* bm;
     const unsigned short* pre;
     int lo, hi;
+    // labels outside [lo, hi] are clamped onto bit hi - lo + 1, which the
+    // table keeps clear: no range test, no branch
+    __device__ __forceinline__ unsigned offset(int k) const {
+        return min((unsigned)(k - lo), (unsigned)(hi - lo + 1));
+    }
     template <bool PV>
     __device__ __forceinline__ int find(int k) const {
-        const unsigned d = (unsigned)(k - lo);
-        if (d > (unsigned)(hi - lo)) return -1;
+        const unsigned d = offset(k);
         const unsigned w = bm[d >> 5];
         if (!((w >> (d & 31)) & 1u)) return -1;
         if (!PV) return 0;
         return (int)pre[d >> 5] + __popc(w & ((1u << (d & 31)) - 1u));
+    }
+    __device__ __forceinline__ unsigned bit(int k) const {
+        const unsigned d = offset(k);
+        return (bm[d >> 5] >> (d & 31)) & 1u;
     }
     // hit counters by rank (rank < slice <= 4096): one word each, so hits on
     // neighbouring entries never share an atomic's word
@@ -129,6 +138,7 @@ struct HashTab {
             b = (b + 1) & bmask;
         }
     }
+    __device__ __forceinline__ unsigned bit(int k) const { return find<false>(k) >= 0; }
     // hit counters by slot (up to twice the slice): 16 bits each, two a
     // word (a counter never exceeds the tasks of a unit, below 2^16 by the
     // unit size cap)
@@ -159,10 +169,14 @@ __device__ __forceinline__ unsigned hash_buckets(int dp) {
 
 template <bool PV, class Tab>
 __device__ __forceinline__ void probe_one(const Tab& T, int k, unsigned* cnt, unsigned& mine) {
-    const int r = T.template find<PV>(k);
-    if (r >= 0) {
-        ++mine;
-        if (PV) T.credit(cnt, r);
+    if constexpr (!PV) {
+        mine += T.bit(k);
+    } else {
+        const int r = T.template find<PV>(k);
+        if (r >= 0) {
+            ++mine;
+            T.credit(cnt, r);
+        }
     }
 }
 
@@ -363,7 +377,7 @@ struct GraphAcc {
 
 // ---------------------------------------------------------------------------
 // Warp unit: a pivot with |U_j| <= 64 processed by one warp with a private
-// table (a bitmap of <= 4096 labels, or 128 hash slots).
+// table (a bitmap of <= 4095 labels, or 128 hash slots).
 // ---------------------------------------------------------------------------
 template <bool PV>
 __device__ __forceinline__ void warp_unit(const GraphView& G, const Unit& U, unsigned* region,
@@ -375,12 +389,12 @@ __device__ __forceinline__ void warp_unit(const GraphView& G, const Unit& U, uns
     const int lo = G.adj[rb], hi = G.adj[re - 1];
     const int mine = (lane < dp) ? G.adj[rb + lane] : 0;
     const int mine2 = (lane + 32 < dp) ? G.adj[rb + 32 + lane] : 0;
-    const bool bitmap = (int64_t)hi - lo < 32 * kSmallBitWords;
+    const bool bitmap = (int64_t)hi - lo + 1 < 32 * kSmallBitWords;   // labels and the guard bit
     uint64_t uh = 0;
     if (PV)
         for (int s = lane; s < kSmallTable / 2; s += 32) cnt[s] = 0;
     if (bitmap) {
-        const int words = ((hi - lo) >> 5) + 1;
+        const int words = ((hi - lo + 1) >> 5) + 1;
         for (int s = lane; s < words; s += 32) region[s] = 0;
         __syncwarp();
         if (lane < dp) atomicOr(&region[(mine - lo) >> 5], 1u << ((mine - lo) & 31));
@@ -542,12 +556,12 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
     const int64_t re = min64(off_at(G, U.j + 1), rb + slice_max);
     const int dp = (int)(re - rb);
     const int lo = G.adj[rb], hi = G.adj[re - 1];
-    const bool bitmap = (int64_t)hi - lo < 32ll * kBitWords;
+    const bool bitmap = (int64_t)hi - lo + 1 < 32ll * kBitWords;      // labels and the guard bit
     uint64_t uh = 0;
     if (PV)
         for (int s = threadIdx.x; s < kRegionWords / 2; s += blockDim.x) cnt[s] = 0;
     if (bitmap) {
-        const int words = ((hi - lo) >> 5) + 1;
+        const int words = ((hi - lo + 1) >> 5) + 1;
         for (int s = threadIdx.x; s < words; s += blockDim.x) region[s] = 0;
         __syncthreads();
         for (int q = threadIdx.x; q < dp; q += blockDim.x) {

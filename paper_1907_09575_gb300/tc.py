@@ -67,7 +67,7 @@ EXPORTS = ("tc_preprocess", "tc_count", "tc_triangles", "tc_graph_get_stats", "t
            "tc_batch_create", "tc_batch_count", "tc_batch_autotune", "tc_batch_get_count_stats",
            "tc_batch_free", "tc_count_batch", "tc_preprocess_components", "tc_count_components",
            "tc_server_create", "tc_server_now", "tc_server_submit_rmat", "tc_server_poll",
-           "tc_server_drain", "tc_server_get_stats", "tc_server_free")
+           "tc_server_drain", "tc_server_get_stats", "tc_server_free", "tc_release_memory")
 
 TC_STATIC_MAX_PAIRS = 262144
 TC_STATIC_MAX_VERTICES = 65536
@@ -130,6 +130,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tc_graph_get_stats.restype = st
     lib.tc_graph_free.argtypes = [vp]
     lib.tc_graph_free.restype = None
+    lib.tc_release_memory.argtypes = [ctypes.c_int]
+    lib.tc_release_memory.restype = st
     lib.tc_tuning_default.argtypes = [ctypes.POINTER(Tuning)]
     lib.tc_tuning_default.restype = st
     lib.tc_last_error.argtypes = []
@@ -226,6 +228,12 @@ def profile_read() -> dict:
     _check(load().tc_profile_read(buf, cnt.value, ctypes.byref(cnt)))
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
             for i in range(cnt.value)}
+
+
+def release_memory(device: int = -1) -> None:
+    """tc_release_memory: give back the device memory the library's pool keeps
+    for reuse (device -1: every device)."""
+    _check(load().tc_release_memory(device))
 
 
 def tuning_default() -> Tuning:
