@@ -79,6 +79,8 @@ def parse():
                     help="RMAT scale of the oracle's bounded sample")
     ap.add_argument("--scale", type=int, default=None,
                     help="override the RMAT scale of the workload (small profiling cases)")
+    ap.add_argument("--no-per-vertex", action="store_true",
+                    help="count totals only (profiling the totals kernel; not the workload's metric)")
     ap.add_argument("--graphs", type=int, default=None,
                     help="override the number of graphs of the batch workload")
     ap.add_argument("--serve-rate", type=float, default=None, help="requests/s (serve workload)")
@@ -173,10 +175,11 @@ def source_digest(kernel: str = "k_count") -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel: str, workload: str, units: float):
+def traffic_for(kernel: str, workload: str, units: float, per_vertex: bool = True):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
-    by units processed when the capture was a smaller case; None when absent
-    or when the kernel sources changed since the capture."""
+    by units processed when the capture was a smaller case; None when absent,
+    when the kernel sources changed since the capture, or when the capture was
+    of the other instance (per-vertex or totals only)."""
     try:
         with open(TRAFFIC_FILE) as f:
             rec = json.load(f)
@@ -185,6 +188,8 @@ def traffic_for(kernel: str, workload: str, units: float):
     e = rec.get(kernel)
     if not e or e.get("source_digest") != source_digest(kernel):
         return None, "kernel changed since the ncu capture" if e else "no capture of this kernel"
+    if bool(e.get("per_vertex", True)) != bool(per_vertex):
+        return None, "capture was of the other count instance"
     per_unit = e["dram_bytes"] / max(e["units"], 1)
     return per_unit * units, f"ncu capture of {e['case']} scaled by units ({e['unit_name']})"
 
@@ -384,7 +389,7 @@ def run_ours(args, wl):
         b_launch = alg_bytes_count(kst, facts["offset_bytes"])
         avg_ms = kms / klaunch
         achieved = b_launch / (avg_ms / 1e3) / 1e9
-        traffic, tnote = traffic_for(kname, args.workload, sum(kst["probes"]))
+        traffic, tnote = traffic_for(kname, args.workload, sum(kst["probes"]), wl["per_vertex"])
         roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                 "traffic_note": tnote, "peak_source": peak_src,
@@ -778,6 +783,10 @@ def main():
         wl["scale"] = args.scale
         wl["desc"] = f"{wl['desc']} [scale overridden to {args.scale}]"
         args.workload = f"{args.workload}@scale{args.scale}"
+    if args.no_per_vertex and "per_vertex" in wl:
+        wl["per_vertex"] = False
+        wl["desc"] = f"{wl['desc']} [totals only]"
+        args.workload = f"{args.workload}@totals"
     if args.impl == "reference":
         run_reference(args, wl)
     elif wl["kind"] == "batch":

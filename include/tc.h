@@ -81,7 +81,10 @@ typedef struct {
     int32_t cta_unit_tasks;    /* tasks per CTA unit (<= 8192) */
     int32_t cta_threads;       /* threads per CTA of the large-pivot kernel (64..256) */
     int32_t slice_max;         /* pivot entries tabled at once by one CTA (64..4096) */
-    int32_t reserved[3];
+    int32_t table_mode;        /* 0: a bitmap when the pivot's label span fits (the
+                                  direct-index case of Section 5.2), else a hash;
+                                  1: hash tables only (the hashed-pivot ablation) */
+    int32_t reserved[2];
 } tc_tuning;
 
 /* Graph facts, computed during preprocessing. */
@@ -98,6 +101,8 @@ typedef struct {
     int64_t device_bytes;   /* bytes held by the graph's arena */
     int32_t offset_bytes;   /* 4 or 8 */
     int32_t pad;
+    uint64_t probes_ijk;    /* the probes of the <i,j,k> order (Section 3.1):
+                               sum over (i,j) in U of |U_j| = sum_j d-(j) d+(j) */
 } tc_graph_stats;
 
 /*

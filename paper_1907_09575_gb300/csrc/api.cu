@@ -103,6 +103,7 @@ void tuning_resolve(const tc_tuning* in, tc_tuning* out) {
         out->cta_threads = (th / 32) * 32;
     }
     if (in->slice_max > 0) out->slice_max = std::max(64, std::min(in->slice_max, kMaxSlice));
+    out->table_mode = in->table_mode == 1 ? 1 : 0;
 }
 
 bool tuning_equal(const tc_tuning& a, const tc_tuning& b) {

@@ -381,15 +381,15 @@ struct GraphAcc {
 // ---------------------------------------------------------------------------
 template <bool PV>
 __device__ __forceinline__ void warp_unit(const GraphView& G, const Unit& U, unsigned* region,
-                                          unsigned* cnt, int64_t* s_base, uint64_t& hits,
-                                          uint64_t& probes, uint64_t& staged) {
+                                          unsigned* cnt, int64_t* s_base, bool hash_only,
+                                          uint64_t& hits, uint64_t& probes, uint64_t& staged) {
     const int lane = threadIdx.x & 31;
     const int64_t rb = off_at(G, U.j), re = off_at(G, U.j + 1);
     const int dp = (int)(re - rb);
     const int lo = G.adj[rb], hi = G.adj[re - 1];
     const int mine = (lane < dp) ? G.adj[rb + lane] : 0;
     const int mine2 = (lane + 32 < dp) ? G.adj[rb + 32 + lane] : 0;
-    const bool bitmap = (int64_t)hi - lo + 1 < 32 * kSmallBitWords;   // labels and the guard bit
+    const bool bitmap = !hash_only && (int64_t)hi - lo + 1 < 32 * kSmallBitWords;   // labels + guard bit
     uint64_t uh = 0;
     if (PV)
         for (int s = lane; s < kSmallTable / 2; s += 32) cnt[s] = 0;
@@ -550,13 +550,13 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
                                          unsigned* region, unsigned* cnt, int* s_ctl,
                                          int64_t* s_base, unsigned short* s_long,
                                          unsigned* s_wsum, unsigned long long* s_red,
-                                         uint64_t& hits, uint64_t& probes) {
+                                         bool hash_only, uint64_t& hits, uint64_t& probes) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int64_t rb = off_at(G, U.j) + (int64_t)U.slice * slice_max;
     const int64_t re = min64(off_at(G, U.j + 1), rb + slice_max);
     const int dp = (int)(re - rb);
     const int lo = G.adj[rb], hi = G.adj[re - 1];
-    const bool bitmap = (int64_t)hi - lo + 1 < 32ll * kBitWords;      // labels and the guard bit
+    const bool bitmap = !hash_only && (int64_t)hi - lo + 1 < 32ll * kBitWords;   // labels + guard bit
     uint64_t uh = 0;
     if (PV)
         for (int s = threadIdx.x; s < kRegionWords / 2; s += blockDim.x) cnt[s] = 0;
@@ -641,7 +641,7 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
 template <bool PV>
 __global__ void __launch_bounds__(256, TC_LARGE_MINB)
     k_count(const GraphView* __restrict__ views, const Unit* __restrict__ large, int64_t nlarge,
-            const Unit* __restrict__ small, int64_t nsmall, int slice_max,
+            const Unit* __restrict__ small, int64_t nsmall, int slice_max, int table_mode,
             unsigned long long* __restrict__ ctr) {
     extern __shared__ __align__(16) unsigned smem[];
     __shared__ long long s_unit;
@@ -672,8 +672,8 @@ __global__ void __launch_bounds__(256, TC_LARGE_MINB)
         const Unit U = large[u];
         const GraphView G = views[U.g];
         acc.to(unit_target(G, U));
-        cta_unit<PV>(G, U, slice_max, region, cnt, s_ctl, s_base, s_long, s_wsum, s_red, acc.hits,
-                     probes);
+        cta_unit<PV>(G, U, slice_max, region, cnt, s_ctl, s_base, s_long, s_wsum, s_red,
+                     table_mode == 1, acc.hits, probes);
         if (threadIdx.x == 0) {
             s_work[1] += 1;
             s_work[3] += (unsigned long long)(U.t1 - U.t0);
@@ -699,7 +699,7 @@ __global__ void __launch_bounds__(256, TC_LARGE_MINB)
             const Unit U = small[u];
             const GraphView G = views[U.g];
             acc.to(unit_target(G, U));
-            warp_unit<PV>(G, U, wregion, wcnt, s_base, acc.hits, probes, staged);
+            warp_unit<PV>(G, U, wregion, wcnt, s_base, table_mode == 1, acc.hits, probes, staged);
             if (lane == 0) {
                 atomicAdd(&s_work[0], 1ull);
                 atomicAdd(&s_work[2], (unsigned long long)(U.t1 - U.t0));
@@ -907,7 +907,7 @@ void launch_count_raw(const CountLaunch& c, const GraphView* views_dev, const Un
     if (L.nlarge + L.nsmall == 0) return;
     auto kern = c.pv ? k_count<true> : k_count<false>;
     kern<<<c.grid, c.threads, c.smem, st>>>(views_dev, L.large, L.nlarge, L.small, L.nsmall,
-                                            t.slice_max, ctr);
+                                            t.slice_max, t.table_mode, ctr);
     TC_LAUNCH_CHECK();
 }
 

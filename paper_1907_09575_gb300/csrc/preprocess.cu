@@ -96,12 +96,16 @@ __global__ void k_degree_keys(const int32_t* __restrict__ deg, int64_t n, int bi
         keys[v] = ((uint64_t)(uint32_t)deg[v] << bits) | (uint64_t)v;
 }
 
+// perm[old id] = rank; degn[rank] = degree (the key's high bits)
 __global__ void k_perm(const uint64_t* __restrict__ sorted, int64_t n, int bits,
-                       int32_t* __restrict__ perm) {
+                       int32_t* __restrict__ perm, int32_t* __restrict__ degn) {
     const uint64_t mask = (1ull << bits) - 1ull;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
-         r += (int64_t)gridDim.x * blockDim.x)
-        perm[sorted[r] & mask] = (int32_t)r;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = sorted[r];
+        perm[k & mask] = (int32_t)r;
+        degn[r] = (int32_t)(k >> bits);
+    }
 }
 
 __global__ void k_orient(const uint64_t* __restrict__ E, int64_t m, int bits,
@@ -138,27 +142,41 @@ __global__ void k_store_offsets(const int64_t* __restrict__ off64, int64_t count
         out[v] = (OffT)off64[v];
 }
 
-// Task (i,j): edge e of U, row i, column j, with len = entries of U_i after j.
+// Task (i,j): edge e of U, row i, column j, with len = entries of U_i after j
+// (> 0).  The tasks of pivot j are the edges of U that end at j -- its
+// in-degree d-(j) = deg(j) - d+(j) -- less the rows whose last entry is j.
+// Also sums the probes the <i,j,k> order would make, sum_j d-(j) d+(j).
 template <class OffT>
-__global__ void k_task_count(const uint64_t* __restrict__ keys, int64_t m, int bits,
-                             const OffT* __restrict__ off, int32_t* __restrict__ tcount,
-                             unsigned long long* __restrict__ probes) {
-    const uint64_t mask = (1ull << bits) - 1ull;
+__global__ void k_task_count_in(const int32_t* __restrict__ degn, const OffT* __restrict__ off,
+                                int64_t n, int32_t* __restrict__ tcount,
+                                unsigned long long* __restrict__ probes_ijk) {
     unsigned long long my = 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < m; base += stride) {
-        int64_t e = base + threadIdx.x;
-        bool has = false;
-        int32_t j = 0;
-        if (e < m) {
-            uint64_t k = keys[e];
-            int64_t i = (int64_t)(k >> bits);
-            j = (int32_t)(k & mask);
-            int64_t len = (int64_t)off[i + 1] - e - 1;
-            has = len > 0;
-            my += (unsigned long long)(len > 0 ? len : 0);
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t dp = (int32_t)(off[v + 1] - off[v]);
+        const int32_t din = degn[v] - dp;
+        tcount[v] = din;
+        my += (unsigned long long)din * (unsigned long long)dp;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) my += __shfl_xor_sync(0xffffffffu, my, o);
+    if ((threadIdx.x & 31) == 0 && my) atomicAdd(probes_ijk, my);
+}
+
+// ... and drop each row's last entry; probes = sum over rows of C(d+(i), 2)
+template <class OffT>
+__global__ void k_task_count_last(const OffT* __restrict__ off, const int32_t* __restrict__ adj,
+                                  int64_t n, int32_t* __restrict__ tcount,
+                                  unsigned long long* __restrict__ probes) {
+    unsigned long long my = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t re = (int64_t)off[i + 1];
+        const int64_t d = re - (int64_t)off[i];
+        if (d > 0) {
+            atomicSub(&tcount[adj[re - 1]], 1);
+            my += (unsigned long long)(d * (d - 1) / 2);
         }
-        if (has) atomicAdd(&tcount[j], 1);
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) my += __shfl_xor_sync(0xffffffffu, my, o);
@@ -167,7 +185,10 @@ __global__ void k_task_count(const uint64_t* __restrict__ keys, int64_t m, int b
 
 // fill[j] starts at the first task slot of pivot j and is advanced
 // atomically; each thread keeps kFillILP edges' atomics in flight at once.
-constexpr int kFillILP = 4;
+#ifndef TC_FILL_ILP
+#define TC_FILL_ILP 4
+#endif
+constexpr int kFillILP = TC_FILL_ILP;
 
 template <class OffT>
 __global__ void k_task_fill(const uint64_t* __restrict__ keys, int64_t m, int bits,
@@ -395,12 +416,11 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
         radix_sort_u64(&dkeys, &dalt, n, bits, bits + dbits, al, st, scal.get());
         {
             Prof prof_("k_perm", st);
-            k_perm<<<grid_for(n, kT, G), kT, 0, st>>>(dkeys, n, bits, g->perm);
+            k_perm<<<grid_for(n, kT, G), kT, 0, st>>>(dkeys, n, bits, g->perm, deg.get());
         }
         TC_LAUNCH_CHECK();
     }
     g->stats.max_deg = maxdeg;
-    deg.release();
     if (num_comps > 0 && n > 0) {
         Prof prof_("k_comp_new", st);
         k_comp_new<<<grid_for(n, kT, G), kT, 0, st>>>(g->perm, n, vpre.get(), num_comps, g->comp);
@@ -439,25 +459,32 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
     }
 
     // a6 tasks grouped by pivot j
-    Buf<unsigned long long> probes(al, 1);
-    TC_CUDA(cudaMemsetAsync(probes.get(), 0, sizeof(unsigned long long), st));
+    Buf<unsigned long long> probes(al, 2);   // [0] <j,i,k> probes, [1] <i,j,k> probes
+    TC_CUDA(cudaMemsetAsync(probes.get(), 0, 2 * sizeof(unsigned long long), st));
     int32_t* tcount = dplus.get();  // reuse
-    TC_CUDA(cudaMemsetAsync(tcount, 0, sizeof(int32_t) * std::max<int64_t>(n, 1), st));
-    if (m > 0) {
-        if (g->off64)
-            {
-                Prof prof_("k_task_count", st);
-                k_task_count<int64_t><<<grid_for(m, kT, G), kT, 0, st>>>(
-                keys, m, bits, static_cast<const int64_t*>(g->off), tcount, probes.get());
-            }
-        else
-            {
-                Prof prof_("k_task_count", st);
-                k_task_count<int32_t><<<grid_for(m, kT, G), kT, 0, st>>>(
-                keys, m, bits, static_cast<const int32_t*>(g->off), tcount, probes.get());
-            }
+    if (n > 0) {
+        {
+            Prof prof_("k_task_count_in", st);
+            if (g->off64)
+                k_task_count_in<int64_t><<<grid_for(n, kT, G), kT, 0, st>>>(
+                    deg.get(), static_cast<const int64_t*>(g->off), n, tcount, probes.get() + 1);
+            else
+                k_task_count_in<int32_t><<<grid_for(n, kT, G), kT, 0, st>>>(
+                    deg.get(), static_cast<const int32_t*>(g->off), n, tcount, probes.get() + 1);
+        }
+        TC_LAUNCH_CHECK();
+        {
+            Prof prof_("k_task_count_last", st);
+            if (g->off64)
+                k_task_count_last<int64_t><<<grid_for(n, kT, G), kT, 0, st>>>(
+                    static_cast<const int64_t*>(g->off), g->adj, n, tcount, probes.get());
+            else
+                k_task_count_last<int32_t><<<grid_for(n, kT, G), kT, 0, st>>>(
+                    static_cast<const int32_t*>(g->off), g->adj, n, tcount, probes.get());
+        }
         TC_LAUNCH_CHECK();
     }
+    deg.release();
     exclusive_scan_i32_to_i64(tcount, g->loff, n, g->loff + n, al, st);
     if (m > 0) {
         Buf<unsigned long long> fill(al, (size_t)std::max<int64_t>(n, 1));
@@ -519,12 +546,12 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
     TC_CUDA(cudaMemcpyAsync(gvpre.get(), hv, sizeof(hv), cudaMemcpyHostToDevice, st));
     UnitPlan plan;
     plan_units(plan, g->view, gvpre.get(), 1, n, def, al, st);
-    unsigned long long hprobes = 0;
+    unsigned long long hprobes[2] = {0, 0};
     int64_t ntasks = 0, ns = 0, nl = 0;
     int herr = 0;
     TC_CUDA(cudaMemcpyAsync(&maxout, scal.get() + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
     TC_CUDA(cudaMemcpyAsync(&herr, scal.get(), sizeof(int), cudaMemcpyDeviceToHost, st));
-    TC_CUDA(cudaMemcpyAsync(&hprobes, probes.get(), sizeof(hprobes), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaMemcpyAsync(hprobes, probes.get(), sizeof(hprobes), cudaMemcpyDeviceToHost, st));
     TC_CUDA(cudaMemcpyAsync(&ntasks, g->loff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     TC_CUDA(cudaMemcpyAsync(&ns, plan.ps.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     TC_CUDA(cudaMemcpyAsync(&nl, plan.pl.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -533,7 +560,8 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
     g->n_tasks = ntasks;
     g->stats.max_outdeg = maxout;
     g->stats.tasks = ntasks;
-    g->stats.probes = hprobes;
+    g->stats.probes = hprobes[0];
+    g->stats.probes_ijk = hprobes[1];
     g->stats.offset_bytes = (int32_t)ob;
     UnitLists L = fill_units(plan, ns, nl, al, st);
     adopt_units(g, L, def);

@@ -38,7 +38,8 @@ class TCError(RuntimeError):
 class Tuning(ctypes.Structure):
     _fields_ = [("small_max_outdeg", ctypes.c_int32), ("warp_unit_tasks", ctypes.c_int32),
                 ("cta_unit_tasks", ctypes.c_int32), ("cta_threads", ctypes.c_int32),
-                ("slice_max", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("slice_max", ctypes.c_int32), ("table_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class GraphStats(ctypes.Structure):
@@ -47,7 +48,7 @@ class GraphStats(ctypes.Structure):
                 ("tasks", ctypes.c_int64), ("probes", ctypes.c_uint64),
                 ("small_units", ctypes.c_int64), ("large_units", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("offset_bytes", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("pad", ctypes.c_int32), ("probes_ijk", ctypes.c_uint64)]
 
 
 class Allocator(ctypes.Structure):

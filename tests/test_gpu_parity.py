@@ -56,6 +56,7 @@ def check(tc, src, dst, n, **kw):
     assert gst["max_outdeg"] == st["max_outdeg"]
     assert gst["max_deg"] == st["max_deg"]
     assert gst["probes"] == st["wedges_jik"]
+    assert gst["probes_ijk"] == st["wedges_ijk"]
     return want
 
 
@@ -210,6 +211,8 @@ TUNINGS = [
     dict(warp_unit_tasks=1, cta_unit_tasks=1),     # one task per unit
     dict(cta_threads=1024, cta_unit_tasks=100000), # one unit per pivot, big CTAs
     dict(cta_threads=64, slice_max=100),
+    dict(table_mode=1),                            # hash tables only
+    dict(table_mode=1, small_max_outdeg=1, slice_max=64),
 ]
 
 
