@@ -43,6 +43,11 @@ static cudaMemPool_t library_pool(int dev) {
         TC_CUDA(cudaMemPoolCreate(&pool, &props));
         uint64_t keep = ~0ull;
         TC_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        // a block freed on another stream is reused only once its free has
+        // completed, never by making this stream wait for that one: the
+        // serving workers' streams stay independent
+        int no = 0;
+        TC_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no));
         g_pool[dev] = pool;
     }
     return g_pool[dev];

@@ -90,19 +90,26 @@ __global__ void __launch_bounds__(kThreads) k_digit_hist(const uint64_t* __restr
     }
 }
 
-// hist[pass][digit] -> exclusive prefix over digits, per pass (one warp per pass).
-__global__ void k_digit_offsets(unsigned long long* __restrict__ hist, int npass) {
+// hist[pass][digit] -> exclusive prefix over digits, per pass: one block of
+// kRadix threads per pass, a thread per digit.
+__global__ void __launch_bounds__(kRadix) k_digit_offsets(unsigned long long* __restrict__ hist, int npass) {
+    __shared__ unsigned long long wsum[kRadix / 32];
     const int p = blockIdx.x;
     if (p >= npass) return;
     unsigned long long* h = hist + (size_t)p * kRadix;
-    if (threadIdx.x == 0) {
-        unsigned long long run = 0;
-        for (int d = 0; d < kRadix; ++d) {
-            const unsigned long long c = h[d];
-            h[d] = run;
-            run += c;
-        }
+    const int d = threadIdx.x, lane = d & 31, w = d >> 5;
+    const unsigned long long c = h[d];
+    unsigned long long inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
     }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    unsigned long long before = 0;
+    for (int q = 0; q < w; ++q) before += wsum[q];
+    h[d] = before + inc - c;
 }
 
 __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint64_t* __restrict__ in,
@@ -252,7 +259,7 @@ void radix_sort_u64(uint64_t** keys, uint64_t** alt, int64_t count, int lo, int 
     TC_LAUNCH_CHECK();
     {
         Prof prof_("k_digit_offsets", st);
-        k_digit_offsets<<<npass, 32, 0, st>>>(hist.get(), npass);
+        k_digit_offsets<<<npass, kRadix, 0, st>>>(hist.get(), npass);
     }
     TC_LAUNCH_CHECK();
     for (int p = 0; p < npass; ++p) {
