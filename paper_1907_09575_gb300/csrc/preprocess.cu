@@ -1,8 +1,14 @@
 // tc_preprocess: Section 5.3 of the paper on one device.
 //
-//   a1 canonicalise   pairs -> key (min << b | max); self-loops -> sentinel
-//   a2 sort + unique  LSD radix sort, keep first of each run -> E (m edges)
-//   a3 degrees        d(v) over E (warp-aggregated atomics)
+//   a1 canonicalise   pairs -> key (min << b | max); self-loops dropped
+//   a2 unique         up to 2^26 pairs: keys inserted into a device hash set
+//                     (open addressing, load <= 1/2) whose compacted slots
+//                     are E, in no particular order (a5 sorts them).  Larger
+//                     inputs: LSD radix sort, first of each run kept -- the
+//                     set's random atomics into a table of 2^31 slots ran
+//                     slower than the sort's passes (measured at 2^30 pairs).
+//   a3 degrees        d(v) counted when a key enters the set / from the
+//                     unique runs
 //   a4 relabel        stable sort of (d(v) << b | v) on the degree bits: the
 //                     rank is the new label (non-decreasing degree, ties by id)
 //   a5 orient + CSR   (min, max) of the new labels, sorted -> U rows ascending
@@ -19,6 +25,111 @@ namespace tc {
 namespace {
 
 constexpr int kT = 256;
+
+constexpr uint64_t kEmptyKey = ~0ull;   // no key: keys use 2b <= 62 bits
+constexpr int64_t kHashDedupMaxPairs = 1ll << 26;   // table of at most 2^27 slots (1 GB)
+
+// a bijective 64-bit mixer (the finaliser of splitmix64, Steele, Lea and
+// Flood 2014) spreading the keys over the table
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    x ^= x >> 30;
+    x *= 0xbf58476d1ce4e5b9ull;
+    x ^= x >> 27;
+    x *= 0x94d049bb133111ebull;
+    x ^= x >> 31;
+    return x;
+}
+
+// a1 + a2 + a3: pair -> canonical key -> hash set; the pair that inserts a
+// key counts it in the degrees of both ends.  Ids outside [0, n) set error
+// bit 1 and are skipped.  The table (capacity cmask + 1 >= 2 * pairs) never
+// fills, so a probe sequence always ends; it is bounded all the same.
+__global__ void k_dedup_insert(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                               int64_t P, int64_t n, int bits, unsigned long long* __restrict__ table,
+                               uint64_t cmask, int32_t* __restrict__ deg, int* __restrict__ err) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = src[e], b = dst[e];
+        if (a < 0 || b < 0 || (int64_t)a >= n || (int64_t)b >= n) {
+            atomicOr(err, 1);
+            continue;
+        }
+        if (a == b) continue;
+        const int32_t lo = min(a, b), hi = max(a, b);
+        const unsigned long long key = ((unsigned long long)lo << bits) | (unsigned long long)hi;
+        uint64_t h = mix64(key) & cmask;
+        for (uint64_t probe = 0; probe <= cmask; ++probe) {
+            const unsigned long long prev = atomicCAS(&table[h], kEmptyKey, key);
+            if (prev == kEmptyKey) {
+                atomicAdd(&deg[lo], 1);
+                atomicAdd(&deg[hi], 1);
+                break;
+            }
+            if (prev == key) break;
+            h = (h + 1) & cmask;
+        }
+    }
+}
+
+// The occupied slots of the table -> E.  Each CTA takes chunks of
+// kCompactItems * blockDim slots, ranks its keys with a block scan and
+// reserves their places in E with one atomic on the count.
+constexpr int kCompactItems = 16;
+
+__global__ void __launch_bounds__(256) k_table_compact(const unsigned long long* __restrict__ table,
+                                                       int64_t cap, uint64_t* __restrict__ E,
+                                                       unsigned long long* __restrict__ count) {
+    __shared__ unsigned wsum[8];
+    __shared__ unsigned long long s_base;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t chunk = (int64_t)kCompactItems * blockDim.x;
+    for (int64_t c0 = (int64_t)blockIdx.x * chunk; c0 < cap; c0 += (int64_t)gridDim.x * chunk) {
+        unsigned long long k[kCompactItems];
+        unsigned mine = 0;
+#pragma unroll
+        for (int u = 0; u < kCompactItems; ++u) {
+            const int64_t s = c0 + (int64_t)u * blockDim.x + threadIdx.x;
+            k[u] = s < cap ? table[s] : kEmptyKey;
+            mine += k[u] != kEmptyKey;
+        }
+        unsigned inc = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) wsum[w] = inc;
+        __syncthreads();
+        unsigned before = 0, total = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+            if (q < w) before += wsum[q];
+            total += wsum[q];
+        }
+        if (threadIdx.x == 0) s_base = total ? atomicAdd(count, (unsigned long long)total) : 0ull;
+        __syncthreads();
+        unsigned long long at = s_base + before + inc - mine;
+#pragma unroll
+        for (int u = 0; u < kCompactItems; ++u)
+            if (k[u] != kEmptyKey) E[at++] = k[u];
+        __syncthreads();   // wsum and s_base are rewritten by the next chunk
+    }
+}
+
+// counter[v] += 1 for the active lanes, whose v are non-decreasing across the
+// warp: one atomic per run of equal v among neighbouring active lanes (an
+// inactive lane splits a run; both parts are added).  All 32 lanes call it.
+__device__ __forceinline__ void warp_add_sorted(int32_t* counter, int32_t v, bool active) {
+    const int lane = threadIdx.x & 31;
+    const int32_t pv = __shfl_up_sync(0xffffffffu, v, 1);
+    const bool pa = __shfl_up_sync(0xffffffffu, active, 1);
+    const bool cont = active && lane > 0 && pa && pv == v;
+    const unsigned C = __ballot_sync(0xffffffffu, cont);   // lanes continuing a run
+    if (active && !cont) {
+        // run length: 1 + the continuation lanes right after this one
+        const unsigned rest = lane == 31 ? 0u : (C >> (lane + 1));
+        atomicAdd(&counter[v], 1 + __ffs(~rest) - 1);
+    }
+}
 
 __global__ void k_canon(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
                         int64_t P, int64_t n, int bits, uint64_t sentinel,
@@ -47,22 +158,6 @@ __global__ void k_unique_flags(const uint64_t* __restrict__ keys, int64_t P, uin
 }
 
 // Adds c to counter[v] once per group of lanes holding the same v.
-// counter[v] += 1 for the active lanes, whose v are non-decreasing across the
-// warp: one atomic per run of equal v among neighbouring active lanes (an
-// inactive lane splits a run; both parts are added).  All 32 lanes call it.
-__device__ __forceinline__ void warp_add_sorted(int32_t* counter, int32_t v, bool active) {
-    const int lane = threadIdx.x & 31;
-    const int32_t pv = __shfl_up_sync(0xffffffffu, v, 1);
-    const bool pa = __shfl_up_sync(0xffffffffu, active, 1);
-    const bool cont = active && lane > 0 && pa && pv == v;
-    const unsigned C = __ballot_sync(0xffffffffu, cont);   // lanes continuing a run
-    if (active && !cont) {
-        // run length: 1 + the continuation lanes right after this one
-        const unsigned rest = lane == 31 ? 0u : (C >> (lane + 1));
-        atomicAdd(&counter[v], 1 + __ffs(~rest) - 1);
-    }
-}
-
 __global__ void k_unique_compact(const uint64_t* __restrict__ keys, const int32_t* __restrict__ flags,
                                  const int64_t* __restrict__ pos, int64_t P, int bits,
                                  uint64_t* __restrict__ E, int32_t* __restrict__ deg) {
@@ -277,7 +372,6 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
     Alloc& al = g->alloc;
     const int64_t n = g->n;
     const int bits = g->bits;
-    const uint64_t sentinel = (bits * 2 >= 64) ? ~0ull : ((1ull << (2 * bits)) - 1ull);
     const unsigned G = (unsigned)(num_sms() * 8);
 
     // input on the device
@@ -304,15 +398,46 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
     }
     Buf<int64_t> tot(al, 4);  // [0] m, [1] tasks
 
-    // a1 + a2: canonical keys, sorted, unique
+    // a1 + a2 + a3
     Buf<uint64_t> kb(al, (size_t)std::max<int64_t>(P, 1));
-    Buf<uint64_t> ab(al, (size_t)std::max<int64_t>(P, 1));
     uint64_t* keys = kb.get();
-    uint64_t* alt = ab.get();
+    Buf<uint64_t> ab;            // second key buffer: the sort's, or allocated for a5
+    uint64_t* alt = nullptr;
     int64_t m = 0;
     Buf<int32_t> deg(al, (size_t)std::max<int64_t>(n, 1));
     TC_CUDA(cudaMemsetAsync(deg.get(), 0, sizeof(int32_t) * std::max<int64_t>(n, 1), st));
-    if (P > 0) {
+    TC_CUDA(cudaMemsetAsync(tot.get(), 0, sizeof(int64_t), st));
+    if (P > 0 && P <= kHashDedupMaxPairs) {
+        // canonical keys into a hash set, degrees on first insert, the set
+        // compacted into E
+        int64_t cap = 1024;
+        while (cap < 2 * P) cap <<= 1;
+        Buf<unsigned long long> table(al, (size_t)cap);
+        TC_CUDA(cudaMemsetAsync(table.get(), 0xff, sizeof(unsigned long long) * (size_t)cap, st));
+        {
+            Prof prof_("k_dedup_insert", st);
+            k_dedup_insert<<<grid_for(P, kT, G), kT, 0, st>>>(src, dst, P, n, bits, table.get(),
+                                                              (uint64_t)(cap - 1), deg.get(), scal.get());
+        }
+        TC_LAUNCH_CHECK();
+        if (num_comps > 0) {
+            Prof prof_("k_check_comp", st);
+            k_check_comp<<<grid_for(P, kT, G), kT, 0, st>>>(src, dst, P, vpre.get(), num_comps, scal.get());
+        }
+        TC_LAUNCH_CHECK();
+        hsrc.release();
+        hdst.release();
+        {
+            Prof prof_("k_table_compact", st);
+            k_table_compact<<<grid_for(cap, kT * kCompactItems, G), kT, 0, st>>>(
+                table.get(), cap, keys, reinterpret_cast<unsigned long long*>(tot.get()));
+        }
+        TC_LAUNCH_CHECK();
+    } else if (P > 0) {
+        // canonical keys, radix sorted, first of each run kept
+        const uint64_t sentinel = (bits * 2 >= 64) ? ~0ull : ((1ull << (2 * bits)) - 1ull);
+        ab = Buf<uint64_t>(al, (size_t)P);
+        alt = ab.get();
         {
             Prof prof_("k_canon", st);
             k_canon<<<grid_for(P, kT, G), kT, 0, st>>>(src, dst, P, n, bits, sentinel, keys, scal.get());
@@ -431,6 +556,10 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
     Buf<int32_t> dplus(al, (size_t)std::max<int64_t>(n, 1));
     TC_CUDA(cudaMemsetAsync(dplus.get(), 0, sizeof(int32_t) * std::max<int64_t>(n, 1), st));
     Buf<int64_t> off64(al, (size_t)(n + 1));
+    if (!alt) {
+        ab = Buf<uint64_t>(al, (size_t)std::max<int64_t>(m, 1));
+        alt = ab.get();
+    }
     if (m > 0) {
         {
             Prof prof_("k_orient", st);

@@ -24,7 +24,8 @@ namespace {
 
 // Worst case for TC_STATIC_MAX_PAIRS pairs and TC_STATIC_MAX_VERTICES
 // vertices with every temporary kept (the bump allocator never frees):
-// about 21 MiB; 32 MiB leaves room for alignment.
+// about 22 MiB (the dedup hash table, 2^19 slots = 4 MiB, is the largest
+// single temporary); 32 MiB leaves room for alignment.
 constexpr size_t kStaticScratchBytes = 32ull << 20;
 
 __device__ __align__(256) unsigned char g_tc_static_scratch[kStaticScratchBytes];
