@@ -267,3 +267,32 @@ def test_sort_tile_boundaries(tc, num):
     check(tc, s, d, n)
     hs, hd = inputs.rmat(num, 12, num)
     check(tc, hs, hd, 4096, offsets=64)
+
+
+def test_dedup_paths_agree(tc):
+    """Inputs up to 2^26 pairs are deduplicated through a hash set, larger
+    ones by the radix sort.  The same pairs given twice cross that bound
+    without changing the graph: both paths must build the same graph and
+    counts, and sampled vertices must match the oracle."""
+    num = (1 << 25) + 1000
+    s, d = tc.generate_rmat(11, 21, num)
+    s2, d2 = torch.cat([s, d]), torch.cat([d, s])          # every pair again, reversed
+    assert s.shape[0] <= (1 << 26) < s2.shape[0]
+    n = 1 << 21
+    out = []
+    for a, b in ((s, d), (s2, d2)):
+        g = tc.preprocess(a, b, n)
+        total, t = g.count(per_vertex=True)
+        out.append((total, t.cpu().numpy(), g.stats()))
+        g.free()
+    (t1, pv1, st1), (t2, pv2, st2) = out
+    assert t1 == t2 and np.array_equal(pv1, pv2)
+    for k in ("m", "max_deg", "max_outdeg", "tasks", "probes", "probes_ijk"):
+        assert st1[k] == st2[k], k
+    assert int(pv1.sum()) == 3 * t1
+    hs, hd = inputs.rmat(11, 21, num)
+    deg = np.bincount(hs, minlength=n) + np.bincount(hd, minlength=n)
+    rng = np.random.default_rng(5)
+    pick = rng.choice(np.flatnonzero((deg > 2) & (deg < 300)), size=24, replace=False).astype(np.int32)
+    want = oracle.vertex_triangles(hs, hd, n, pick)
+    assert np.array_equal(pv1[pick].astype(np.uint64), want)
