@@ -93,6 +93,33 @@ def parse():
 # helpers
 # ----------------------------------------------------------------------------
 
+def reduce_over_ranks(maxes, sums, device="cuda"):
+    """Job-wide figures from per-rank ones: the max over ranks of each entry
+    of `maxes` (times) and the sum of each entry of `sums` (work done).  The
+    identity on a single rank (no process group)."""
+    import torch
+    import torch.distributed as dist
+    mx = torch.tensor([float(x) for x in maxes], dtype=torch.float64, device=device)
+    sm = torch.tensor([float(x) for x in sums], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        if mx.numel():
+            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        if sm.numel():
+            dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return [float(x) for x in mx], [float(x) for x in sm]
+
+
+def gather_over_ranks(arr):
+    """The concatenation over ranks (in rank order) of a 1-D numpy array."""
+    import numpy as np
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1):
+        return arr
+    parts = [None] * dist.get_world_size()
+    dist.all_gather_object(parts, arr)
+    return np.concatenate([np.asarray(p) for p in parts])
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -351,15 +378,7 @@ def run_ours(args, wl):
     tc.profile_enable(False)
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
-    t = torch.tensor([ms, float(facts["m"])], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t.clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        ms, m_all = float(tmax[0]), float(tsum[1])
-    else:
-        m_all = float(facts["m"])
+    (ms,), (m_all,) = reduce_over_ranks([ms], [facts["m"]])
     value = m_all / (ms / 1e3)
 
     # --- count alone (the paper's "tct"), CSR resident -------------------
@@ -421,10 +440,7 @@ def run_ours(args, wl):
         torch.cuda.synchronize()
         barrier()
         e2e_s = (time.perf_counter() - t0) / args.steps
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        if ws > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt[0])
+        (e2e_s,), _ = reduce_over_ranks([e2e_s], [])
         e2e_total = r[0] if isinstance(r, tuple) else r
         assert e2e_total == total, (e2e_total, total)
         e2e = {"value": m_all / e2e_s, "unit": "edges/s", "ms_per_step": e2e_s * 1e3,
@@ -567,13 +583,7 @@ def run_batch(args, wl):
     ms_one = ev0.elapsed_time(ev1) / args.steps
     assert torch.equal(per, totals), "one-per-launch totals differ from the batch"
 
-    tt = torch.tensor([ms, ms_one, m_all], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(tt[:2], op=dist.ReduceOp.MAX)
-        msum = tt[2:].clone()
-        dist.all_reduce(msum, op=dist.ReduceOp.SUM)
-        tt[2] = msum[0]
-    ms, ms_one, m_tot = float(tt[0]), float(tt[1]), float(tt[2])
+    (ms, ms_one), (m_tot,) = reduce_over_ranks([ms, ms_one], [m_all])
     value = m_tot / (ms / 1e3)
 
     hbm, peak_src = peaks()
@@ -741,18 +751,23 @@ def run_serve(args, wl):
             assert oracle.count(hs, hd, sp.n) == alone
             checked_oracle += 1
 
+    # job-wide: requests and pairs summed over the replicas, the longest span,
+    # percentiles over every rank's requests
+    (span,), (n_done, pairs) = reduce_over_ranks([span], [len(results), pairs])
+    lat = gather_over_ranks(lat)
+    qwait = gather_over_ranks(qwait)
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
         return
     line = {
         "metric": "served exact triangle counts: throughput with p50/p99 latency",
-        "value": len(results) / span, "unit": "requests/s", "n_gpus": ws, "steps": 1,
+        "value": n_done / span, "unit": "requests/s", "n_gpus": ws, "steps": 1,
         "warmup": args.warmup, "ms_per_step": span * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32 ids / uint64 counts",
         "data": "synthetic (seeded RMAT request specs expanded on the device)",
         "config": {"workload": args.workload, "desc": wl["desc"], "rate_hz": rate,
-                   "seconds": seconds, "requests": len(specs), "pairs": int(pairs),
+                   "seconds": seconds, "requests": int(n_done), "pairs": int(pairs),
                    "workers": args.serve_workers, "hbm_budget_bytes": 64 << 30,
                    "l2": "each tick's pairs and CSRs exceed L2 except for the smallest ticks",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
@@ -763,8 +778,8 @@ def run_serve(args, wl):
                           "p99": float(np.percentile(qwait, 99) * 1e3)},
         "pairs_per_s": pairs / span, "offered_pairs_per_s": pairs / seconds,
         "server": st, "checked": {"standalone_gpu": int(len(sample)), "oracle": checked_oracle},
-        "e2e": {"value": len(results) / span, "unit": "requests/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 8 * len(results),
+        "e2e": {"value": n_done / span, "unit": "requests/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": int(8 * n_done),
                 "note": "requests are generator specs expanded on the device; only totals return"},
         "gpu_launches": launches, "clocks": clocks,
         "kernels_ms": {k: [v[0], round(v[1], 2)] for k, v in
