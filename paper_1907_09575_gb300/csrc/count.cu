@@ -8,9 +8,11 @@
 //
 // Tables (Section 5.2, "Modifying the hashing routine for sparser vertices"):
 // a bitmap over [min U_j, max U_j] when that label span fits (collision
-// free), else buckets of 4 slots with bucket = k AND (buckets - 1).  Probes
-// outside [min U_j, max U_j] are rejected before the lookup, the per-probe
-// form of the early exit of Section 5.2.
+// free), else buckets of 4 slots with bucket = k AND (buckets - 1)
+// (tc_tuning.table_mode = 1 forces buckets everywhere).  A probe outside
+// [min U_j, max U_j] cannot hit -- the per-probe form of the early exit of
+// Section 5.2: a bitmap lookup clamps it onto a guard bit that is always
+// clear, a bucket lookup rejects it before reading the table.
 //
 // Work: units (graph, pivot, slice of U_j, range of tasks).  Pivots with
 // |U_j| <= 64 become warp units (a private table per warp); larger ones CTA
