@@ -90,7 +90,7 @@ void Alloc::put(void* p, size_t bytes) {
 void tuning_defaults(tc_tuning* t) {
     std::memset(t, 0, sizeof(*t));
     t->small_max_outdeg = kSmallMaxOutdeg;
-    t->warp_unit_tasks = 256;
+    t->warp_unit_tasks = 64;    // small warp units keep small graphs spread over the SMs
     t->cta_unit_tasks = 2048;
     t->cta_threads = 256;
     t->slice_max = kMaxSlice;
