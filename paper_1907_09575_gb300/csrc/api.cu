@@ -119,6 +119,7 @@ static void graph_release(tc_graph* g) {
     if (!g) return;
     try {
         if (g->units_mem) g->alloc.put(g->units_mem, g->units_bytes);
+        if (g->tlow) g->alloc.put(g->tlow, g->tlow_bytes);
         if (g->arena) g->alloc.put(g->arena, g->arena_bytes);
     } catch (const Error&) {
     }

@@ -164,6 +164,8 @@ struct tc_graph {
     unsigned long long* comp_totals = nullptr;
     int32_t num_comps = 0;
     uint64_t* tnew = nullptr;   // per-vertex accumulator in new labels, n
+    unsigned* tlow = nullptr;   // 32-bit per-task shares (per-vertex counts), n, on demand
+    size_t tlow_bytes = 0;
 
     int64_t n_tasks = 0, n_small = 0, n_large = 0;
     void* units_mem = nullptr;      // small units, then large units

@@ -31,6 +31,9 @@
 namespace tc {
 namespace {
 
+#ifndef TC_TLOW32
+#define TC_TLOW32 1            // per-task credit into 32-bit counters when they cannot overflow
+#endif
 #ifndef TC_LARGE_MINB
 #define TC_LARGE_MINB 4        // CTAs per SM the CTA kernel's registers must allow
 #endif
@@ -240,6 +243,17 @@ __device__ __forceinline__ unsigned warp_walk_tail(int64_t st, int L, const int3
     }
 }
 
+// A task's hits (i's share of its triangles, at most C(|U_i|, 2)): into the
+// 32-bit counters tlow when the caller provides them (the largest row keeps
+// that share below 2^32; half the bytes of the 64-bit accumulator, so more
+// of the scattered atomics stay in L2), else into tnew.
+__device__ __forceinline__ void credit_task(unsigned long long* tnew, unsigned* tlow, int i, unsigned c) {
+    if (tlow)
+        atomicAdd(&tlow[i], c);
+    else
+        atomicAdd(&tnew[i], (unsigned long long)c);
+}
+
 // ---------------------------------------------------------------------------
 // One warp takes up to 32 tasks [tb, min(tb+32, t1)).
 //
@@ -259,7 +273,7 @@ __device__ __forceinline__ unsigned warp_walk_tail(int64_t st, int L, const int3
 template <bool PV, class Tab>
 __device__ __forceinline__ void warp_probe_group(const Task* __restrict__ tasks, int64_t tb, int64_t t1,
                                                  const int32_t* __restrict__ adj, const Tab& T,
-                                                 unsigned* cnt, unsigned long long* tnew,
+                                                 unsigned* cnt, unsigned long long* tnew, unsigned* tlow,
                                                  int64_t* s_base, int64_t t0, unsigned short* defer,
                                                  int* ndefer, uint64_t& hits, uint64_t& probes) {
     const int lane = threadIdx.x & 31;
@@ -346,7 +360,7 @@ __device__ __forceinline__ void warp_probe_group(const Task* __restrict__ tasks,
         }
     }
     __syncwarp();   // s_base is rewritten by the warp's next group
-    if (PV && valid && c) atomicAdd(&tnew[i], (unsigned long long)c);
+    if (PV && valid && c) credit_task(tnew, tlow, i, c);
 }
 
 __device__ __forceinline__ int64_t off_at(const GraphView& G, int64_t v) {
@@ -383,7 +397,7 @@ struct GraphAcc {
 // ---------------------------------------------------------------------------
 template <bool PV>
 __device__ __forceinline__ void warp_unit(const GraphView& G, const Unit& U, unsigned* region,
-                                          unsigned* cnt, int64_t* s_base, bool hash_only,
+                                          unsigned* cnt, int64_t* s_base, bool hash_only, unsigned* tlow,
                                           uint64_t& hits, uint64_t& probes, uint64_t& staged) {
     const int lane = threadIdx.x & 31;
     const int64_t rb = off_at(G, U.j), re = off_at(G, U.j + 1);
@@ -423,7 +437,7 @@ __device__ __forceinline__ void warp_unit(const GraphView& G, const Unit& U, uns
         __syncwarp();
         const BitTab T{region, pre, lo, hi};
         for (int64_t tb = U.t0; tb < U.t1; tb += 32)
-            warp_probe_group<PV>(G.tasks, tb, U.t1, G.adj, T, cnt, G.tnew, s_base, U.t0, nullptr,
+            warp_probe_group<PV>(G.tasks, tb, U.t1, G.adj, T, cnt, G.tnew, tlow, s_base, U.t0, nullptr,
                                  nullptr, uh, probes);
         __syncwarp();
         if (PV) {
@@ -446,7 +460,7 @@ __device__ __forceinline__ void warp_unit(const GraphView& G, const Unit& U, uns
         __syncwarp();
         const HashTab T{tab, bmask, lo, hi};
         for (int64_t tb = U.t0; tb < U.t1; tb += 32)
-            warp_probe_group<PV>(G.tasks, tb, U.t1, G.adj, T, cnt, G.tnew, s_base, U.t0, nullptr,
+            warp_probe_group<PV>(G.tasks, tb, U.t1, G.adj, T, cnt, G.tnew, tlow, s_base, U.t0, nullptr,
                                  nullptr, uh, probes);
         __syncwarp();
         if (PV)
@@ -474,7 +488,7 @@ __device__ __forceinline__ void warp_unit(const GraphView& G, const Unit& U, uns
 template <bool PV, class Tab>
 __device__ __forceinline__ void cta_probe_unit(const GraphView& G, const Unit& U, const Tab& T,
                                                unsigned* cnt, int* s_ctl, int64_t* s_base,
-                                               unsigned short* s_long, uint64_t& uh,
+                                               unsigned short* s_long, unsigned* tlow, uint64_t& uh,
                                                uint64_t& probes) {
     // s_ctl: [0] next group, [1] deferred long tasks, [2] next long task
     const int lane = threadIdx.x & 31;
@@ -486,7 +500,7 @@ __device__ __forceinline__ void cta_probe_unit(const GraphView& G, const Unit& U
         g = __shfl_sync(0xffffffffu, g, 0);
         const int64_t tb = U.t0 + (int64_t)g * 32;
         if (tb >= U.t1) break;
-        warp_probe_group<PV>(tasks, tb, U.t1, adj, T, cnt, G.tnew, s_base, U.t0, s_long, &s_ctl[1],
+        warp_probe_group<PV>(tasks, tb, U.t1, adj, T, cnt, G.tnew, tlow, s_base, U.t0, s_long, &s_ctl[1],
                              uh, probes);
     }
     __syncthreads();
@@ -540,7 +554,7 @@ __device__ __forceinline__ void cta_probe_unit(const GraphView& G, const Unit& U
             }
             probes += (uint64_t)cur.len;
             const unsigned ch = warp_walk_tail<PV>(cur.start, cur.len, adj, T, cnt, uh);
-            if (lane == 0 && ch) atomicAdd(&G.tnew[cur.i], (unsigned long long)ch);
+            if (lane == 0 && ch) credit_task(G.tnew, tlow, cur.i, ch);
             x = xn;
             cur = nxt;
         }
@@ -552,7 +566,7 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
                                          unsigned* region, unsigned* cnt, int* s_ctl,
                                          int64_t* s_base, unsigned short* s_long,
                                          unsigned* s_wsum, unsigned long long* s_red,
-                                         bool hash_only, uint64_t& hits, uint64_t& probes) {
+                                         bool hash_only, unsigned* tlow, uint64_t& hits, uint64_t& probes) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int64_t rb = off_at(G, U.j) + (int64_t)U.slice * slice_max;
     const int64_t re = min64(off_at(G, U.j + 1), rb + slice_max);
@@ -593,7 +607,7 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
             __syncthreads();
         }
         const BitTab T{region, pre, lo, hi};
-        cta_probe_unit<PV>(G, U, T, cnt, s_ctl, s_base, s_long, uh, probes);
+        cta_probe_unit<PV>(G, U, T, cnt, s_ctl, s_base, s_long, tlow, uh, probes);
         __syncthreads();
         if (PV)
             for (int r = threadIdx.x; r < dp; r += blockDim.x) {
@@ -609,7 +623,7 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
         for (int q = threadIdx.x; q < dp; q += blockDim.x) hash_insert(tab, bmask, G.adj[rb + q]);
         __syncthreads();
         const HashTab T{tab, bmask, lo, hi};
-        cta_probe_unit<PV>(G, U, T, cnt, s_ctl, s_base, s_long, uh, probes);
+        cta_probe_unit<PV>(G, U, T, cnt, s_ctl, s_base, s_long, tlow, uh, probes);
         __syncthreads();
         if (PV)
             for (int s = threadIdx.x; s < 4 * (int)buckets; s += blockDim.x) {
@@ -644,7 +658,7 @@ template <bool PV>
 __global__ void __launch_bounds__(256, TC_LARGE_MINB)
     k_count(const GraphView* __restrict__ views, const Unit* __restrict__ large, int64_t nlarge,
             const Unit* __restrict__ small, int64_t nsmall, int slice_max, int table_mode,
-            unsigned long long* __restrict__ ctr) {
+            unsigned* tlow, unsigned long long* __restrict__ ctr) {
     extern __shared__ __align__(16) unsigned smem[];
     __shared__ long long s_unit;
     __shared__ int s_ctl[4];
@@ -675,7 +689,7 @@ __global__ void __launch_bounds__(256, TC_LARGE_MINB)
         const GraphView G = views[U.g];
         acc.to(unit_target(G, U));
         cta_unit<PV>(G, U, slice_max, region, cnt, s_ctl, s_base, s_long, s_wsum, s_red,
-                     table_mode == 1, acc.hits, probes);
+                     table_mode == 1, tlow, acc.hits, probes);
         if (threadIdx.x == 0) {
             s_work[1] += 1;
             s_work[3] += (unsigned long long)(U.t1 - U.t0);
@@ -701,7 +715,7 @@ __global__ void __launch_bounds__(256, TC_LARGE_MINB)
             const Unit U = small[u];
             const GraphView G = views[U.g];
             acc.to(unit_target(G, U));
-            warp_unit<PV>(G, U, wregion, wcnt, s_base, table_mode == 1, acc.hits, probes, staged);
+            warp_unit<PV>(G, U, wregion, wcnt, s_base, table_mode == 1, tlow, acc.hits, probes, staged);
             if (lane == 0) {
                 atomicAdd(&s_work[0], 1ull);
                 atomicAdd(&s_work[2], (unsigned long long)(U.t1 - U.t0));
@@ -722,12 +736,16 @@ __global__ void __launch_bounds__(256, TC_LARGE_MINB)
     }
 }
 
-__global__ void k_gather_pv(const unsigned long long* __restrict__ tnew,
+// per-vertex counts in original ids: the 64-bit accumulator plus, when used,
+// the 32-bit per-task shares
+__global__ void k_gather_pv(const unsigned long long* __restrict__ tnew, const unsigned* __restrict__ tlow,
                             const int32_t* __restrict__ perm, int64_t n,
                             uint64_t* __restrict__ out) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x)
-        out[v] = tnew[perm[v]];
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t x = perm[v];
+        out[v] = tnew[x] + (tlow ? (uint64_t)tlow[x] : 0ull);
+    }
 }
 
 __global__ void k_copy_total(const unsigned long long* __restrict__ ctr, uint64_t* __restrict__ out) {
@@ -905,23 +923,23 @@ CountLaunch prepare_count(const UnitLists& L, const tc_tuning& t, bool pv) {
 }
 
 void launch_count_raw(const CountLaunch& c, const GraphView* views_dev, const UnitLists& L,
-                      const tc_tuning& t, unsigned long long* ctr, cudaStream_t st) {
+                      const tc_tuning& t, unsigned long long* ctr, cudaStream_t st, unsigned* tlow) {
     if (L.nlarge + L.nsmall == 0) return;
     auto kern = c.pv ? k_count<true> : k_count<false>;
     kern<<<c.grid, c.threads, c.smem, st>>>(views_dev, L.large, L.nlarge, L.small, L.nsmall,
-                                            t.slice_max, t.table_mode, ctr);
+                                            t.slice_max, t.table_mode, tlow, ctr);
     TC_LAUNCH_CHECK();
 }
 
 void launch_count(const GraphView* views_dev, const UnitLists& L, const tc_tuning& t, bool pv,
-                  unsigned long long* ctr, cudaStream_t st, bool profile) {
+                  unsigned long long* ctr, cudaStream_t st, bool profile, unsigned* tlow) {
     if (L.nlarge + L.nsmall == 0) return;
     const CountLaunch c = prepare_count(L, t, pv);
     if (profile) {
         Prof prof_("k_count", st);
-        launch_count_raw(c, views_dev, L, t, ctr, st);
+        launch_count_raw(c, views_dev, L, t, ctr, st, tlow);
     } else {
-        launch_count_raw(c, views_dev, L, t, ctr, st);
+        launch_count_raw(c, views_dev, L, t, ctr, st, tlow);
     }
 }
 
@@ -947,7 +965,7 @@ void count_components(const tc_graph* gc, const tc_tuning& t, uint64_t* comp_tot
     L.small = g->small_units;
     L.nlarge = g->n_large;
     L.nsmall = g->n_small;
-    launch_count(g->view_comp, L, tt, false, g->counters, st, true);
+    launch_count(g->view_comp, L, tt, false, g->counters, st, true, nullptr);
     TC_CUDA(cudaMemcpyAsync(comp_totals_dev, g->comp_totals, sizeof(uint64_t) * (size_t)g->num_comps,
                             cudaMemcpyDeviceToDevice, st));
 }
@@ -960,17 +978,27 @@ void count(const tc_graph* gc, const tc_tuning& t, uint64_t* total_dev, uint64_t
     const bool pv = per_vertex_dev != nullptr;
     TC_CUDA(cudaMemsetAsync(g->counters, 0, sizeof(unsigned long long) * CTR_COUNT, st));
     if (pv && g->n > 0) TC_CUDA(cudaMemsetAsync(g->tnew, 0, sizeof(uint64_t) * (size_t)g->n, st));
+    // a task's share is at most C(max |U_i|, 2): 32-bit counters when that fits
+    const uint64_t dmax = (uint64_t)g->stats.max_outdeg;
+    const bool tlow32 = TC_TLOW32 && pv && g->n > 0 && dmax * (dmax - (dmax > 0)) / 2 < (1ull << 32);
+    if (tlow32) {
+        if (!g->tlow) {
+            g->tlow_bytes = sizeof(unsigned) * (size_t)g->n;
+            g->tlow = static_cast<unsigned*>(g->alloc.get(g->tlow_bytes));
+        }
+        TC_CUDA(cudaMemsetAsync(g->tlow, 0, g->tlow_bytes, st));
+    }
     UnitLists L;
     L.large = g->large_units;
     L.small = g->small_units;
     L.nlarge = g->n_large;
     L.nsmall = g->n_small;
-    launch_count(g->view, L, tt, pv, g->counters, st, true);
+    launch_count(g->view, L, tt, pv, g->counters, st, true, tlow32 ? g->tlow : nullptr);
     if (pv && g->n > 0) {
         {
             Prof prof_("k_gather_pv", st);
             k_gather_pv<<<grid_for(g->n, 256, num_sms() * 8), 256, 0, st>>>(
-                reinterpret_cast<const unsigned long long*>(g->tnew), g->perm, g->n, per_vertex_dev);
+                reinterpret_cast<const unsigned long long*>(g->tnew), tlow32 ? g->tlow : nullptr, g->perm, g->n, per_vertex_dev);
         }
         TC_LAUNCH_CHECK();
     }
