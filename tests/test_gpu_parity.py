@@ -296,3 +296,19 @@ def test_dedup_paths_agree(tc):
     pick = rng.choice(np.flatnonzero((deg > 2) & (deg < 300)), size=24, replace=False).astype(np.int32)
     want = oracle.vertex_triangles(hs, hd, n, pick)
     assert np.array_equal(pv1[pick].astype(np.uint64), want)
+
+
+def test_invalid_id_on_the_sort_path(tc):
+    """Inputs above 2^26 pairs take the radix-sort deduplication; an id
+    outside [0, n) there is reported too, and the library stays usable."""
+    num = (1 << 26) + 10
+    n = 1 << 20
+    s, d = tc.generate_rmat(3, 20, num)
+    s[num // 2] = n + 5
+    with pytest.raises(tc.TCError) as ei:
+        tc.preprocess(s, d, n)
+    assert ei.value.status == tc.TC_EINVAL
+    s[num // 2] = 0
+    g = tc.preprocess(s, d, n)
+    assert g.stats()["m"] > 0 and g.count() > 0
+    g.free()
