@@ -224,6 +224,15 @@ TC_API void tc_graph_free(tc_graph* g);
  * TC_ECUDA. */
 TC_API tc_status tc_release_memory(int device);
 
+/* Self-test of the device's bounded waits (not part of the paper's method).
+ * One warp waits, with the wait the radix sort's look-back uses, for a
+ * device word that nothing ever publishes, polling at most spin_limit times
+ * (1 <= spin_limit <= 2^20, a few ms at most); the wait runs out, the kernel
+ * records it and returns, and the call reports it.  Returns TC_ETIMEOUT --
+ * the expected result -- and leaves the context usable; TC_EINVAL for a
+ * limit out of range; TC_ECUDA.  Synchronises the stream. */
+TC_API tc_status tc_selftest_wait_timeout(int64_t spin_limit, void* stream);
+
 /* Defaults for every tc_tuning field.  TC_EINVAL on NULL. */
 TC_API tc_status tc_tuning_default(tc_tuning* out);
 

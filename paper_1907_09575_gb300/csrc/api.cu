@@ -333,6 +333,18 @@ tc_status tc_count_get_stats(const tc_graph* g, tc_count_stats* out, void* strea
 
 void tc_graph_free(tc_graph* g) { graph_release(g); }
 
+tc_status tc_selftest_wait_timeout(int64_t spin_limit, void* stream) {
+    TC_API_BEGIN
+    if (spin_limit < 1 || spin_limit > (1 << 20))
+        TC_FAIL(TC_EINVAL, "tc_selftest_wait_timeout: spin_limit outside [1, 2^20]");
+    Alloc al;
+    al.stream = static_cast<cudaStream_t>(stream);
+    if (selftest_wait_timeout((long)spin_limit, al, al.stream))
+        TC_FAIL(TC_ETIMEOUT, "tc_selftest_wait_timeout: the bounded wait ran out and reported it");
+    TC_FAIL(TC_ECUDA, "tc_selftest_wait_timeout: the wait ended without its word being published");
+    TC_API_END
+}
+
 tc_status tc_release_memory(int device) {
     TC_API_BEGIN
     if (device >= kMaxDevices) TC_FAIL(TC_EINVAL, "tc_release_memory: device %d out of range", device);

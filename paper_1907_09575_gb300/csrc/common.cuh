@@ -137,6 +137,9 @@ void exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t count,
 // TC_ETIMEOUT itself.
 void radix_sort_u64(uint64_t** keys, uint64_t** alt, int64_t count, int lo, int hi,
                     Alloc& al, cudaStream_t st, int* err_dev = nullptr);
+// One warp waits, with the radix look-back's bounded wait, on a word nothing
+// publishes; true when the bound ran out and was reported (synchronises).
+bool selftest_wait_timeout(long limit, Alloc& al, cudaStream_t st);
 
 }  // namespace tc
 

@@ -59,6 +59,27 @@ __device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long 
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// Waits until the status word *q carries a flag (top two bits), at most
+// `limit` polls; true with the word in v, false when the bound ran out.
+__device__ __forceinline__ bool wait_published(const unsigned long long* q, unsigned long long& v,
+                                               long limit) {
+    v = ld_relaxed(q);
+    long spins = 0;
+    while ((v >> 62) == 0) {
+        if (++spins > limit) return false;
+        __nanosleep(32);
+        v = ld_relaxed(q);
+    }
+    return true;
+}
+
+// One warp waits, bounded, on a word nothing publishes: the look-back's wait
+// running out, error bit 4 set, the kernel returning.
+__global__ void k_wait_selftest(const unsigned long long* word, long limit, int* err) {
+    unsigned long long v;
+    if (!wait_published(word, v, limit) && threadIdx.x == 0) atomicOr(err, 4);
+}
+
 // Global digit counts of every pass: hist[pass][digit], bits [lo, hi).
 __global__ void __launch_bounds__(kThreads) k_digit_hist(const uint64_t* __restrict__ keys,
                                                          int64_t count, int lo, int npass, int hi,
@@ -178,17 +199,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint64_t* __rest
         } else {
             st_relaxed(my, kFlagAgg | (unsigned long long)tot);
             for (int p = tile - 1; p >= 0; --p) {
-                const unsigned long long* q = status + (size_t)p * kRadix + d;
-                unsigned long long v = ld_relaxed(q);
-                long spins = 0;
-                while ((v >> 62) == 0) {
-                    if (++spins > kSpinLimit) {
-                        atomicOr(err, 4);
-                        v = kFlagPre;
-                        break;
-                    }
-                    __nanosleep(32);
-                    v = ld_relaxed(q);
+                unsigned long long v;
+                if (!wait_published(status + (size_t)p * kRadix + d, v, kSpinLimit)) {
+                    atomicOr(err, 4);
+                    break;
                 }
                 excl += v & kValMask;
                 if ((v >> 62) == 2) break;
@@ -282,6 +296,21 @@ void radix_sort_u64(uint64_t** keys, uint64_t** alt, int64_t count, int lo, int 
     TC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     TC_CUDA(cudaStreamSynchronize(st));
     if (herr) TC_FAIL(TC_ETIMEOUT, "radix sort: a look-back wait ran past its bound");
+}
+
+}  // namespace tc
+
+namespace tc {
+
+bool selftest_wait_timeout(long limit, Alloc& al, cudaStream_t st) {
+    Buf<unsigned long long> w(al, 2);   // [0] the word nothing publishes, [1] error flag
+    TC_CUDA(cudaMemsetAsync(w.get(), 0, 2 * sizeof(unsigned long long), st));
+    k_wait_selftest<<<1, 32, 0, st>>>(w.get(), limit, reinterpret_cast<int*>(w.get() + 1));
+    TC_LAUNCH_CHECK();
+    int err = 0;
+    TC_CUDA(cudaMemcpyAsync(&err, w.get() + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    return (err & 4) != 0;
 }
 
 }  // namespace tc

@@ -68,7 +68,8 @@ EXPORTS = ("tc_preprocess", "tc_count", "tc_triangles", "tc_graph_get_stats", "t
            "tc_batch_create", "tc_batch_count", "tc_batch_autotune", "tc_batch_get_count_stats",
            "tc_batch_free", "tc_count_batch", "tc_preprocess_components", "tc_count_components",
            "tc_server_create", "tc_server_now", "tc_server_submit_rmat", "tc_server_poll",
-           "tc_server_drain", "tc_server_get_stats", "tc_server_free", "tc_release_memory")
+           "tc_server_drain", "tc_server_get_stats", "tc_server_free", "tc_release_memory",
+           "tc_selftest_wait_timeout")
 
 TC_STATIC_MAX_PAIRS = 262144
 TC_STATIC_MAX_VERTICES = 65536
@@ -131,6 +132,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tc_graph_get_stats.restype = st
     lib.tc_graph_free.argtypes = [vp]
     lib.tc_graph_free.restype = None
+    lib.tc_selftest_wait_timeout.argtypes = [ctypes.c_int64, vp]
+    lib.tc_selftest_wait_timeout.restype = st
     lib.tc_release_memory.argtypes = [ctypes.c_int]
     lib.tc_release_memory.restype = st
     lib.tc_tuning_default.argtypes = [ctypes.POINTER(Tuning)]
@@ -229,6 +232,12 @@ def profile_read() -> dict:
     _check(load().tc_profile_read(buf, cnt.value, ctypes.byref(cnt)))
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
             for i in range(cnt.value)}
+
+
+def selftest_wait_timeout(spin_limit: int = 4096, stream=None) -> int:
+    """tc_selftest_wait_timeout: the status of a bounded device wait made to
+    run out (TC_ETIMEOUT when the bound works)."""
+    return int(load().tc_selftest_wait_timeout(spin_limit, _stream_ptr(stream)))
 
 
 def release_memory(device: int = -1) -> None:
