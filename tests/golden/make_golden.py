@@ -6,9 +6,14 @@
   implementation in this repository.
 * ``rmat_s14_oracle.json``: the oracle's results on the RMAT scale-14,
   edge-factor-16 graphs of seeds 1, 2, 3 (the small single-graph workload).
-  Only ``oracle/`` and the seeded input generators are called.
+* ``fullsize_oracle.json`` (``--fullsize``, tens of minutes and ~30 GB of
+  host memory): the oracle's results on the two full-size single-graph
+  workloads, RMAT scale 26 (edge factor 16, seed 1) and the Chung-Lu graph
+  (5e7 vertices, seed 1): total, a digest of the per-vertex counts, the
+  graph statistics.
+Only ``oracle/`` and the seeded input generators are called.
 
-Run from the repository root:  python tests/golden/make_golden.py
+Run from the repository root:  python tests/golden/make_golden.py [--fullsize]
 """
 from __future__ import annotations
 
@@ -117,7 +122,37 @@ def rmat_s14():
     return res
 
 
+def _record(spec, src, dst):
+    import oracle
+    total, t, st = oracle.count(src, dst, spec.n, per_vertex=True, stats=True)
+    return dict(n=spec.n, num_pairs=int(src.shape[0]), total=total,
+                per_vertex_sha256=hashlib.sha256(t.astype("<u8").tobytes()).hexdigest(),
+                per_vertex_sum=int(t.sum(dtype="u8")), per_vertex_max=int(t.max()),
+                per_vertex_head=[int(x) for x in t[:32]], **st,
+                pairs_sha256=hashlib.sha256(src.astype("<i4").tobytes()
+                                            + dst.astype("<i4").tobytes()).hexdigest())
+
+
+def fullsize():
+    from paper_1907_09575_gb300 import inputs
+    res = {}
+    spec = inputs.rmat_graph(1, 26, 16)
+    src, dst = spec.generate()
+    res["rmat-s26"] = _record(spec, src, dst)
+    del src, dst
+    spec = inputs.chung_lu_graph(1)
+    src, dst = spec.generate()
+    res["chunglu"] = _record(spec, src, dst)
+    return res
+
+
 if __name__ == "__main__":
+    if "--fullsize" in sys.argv:
+        out = fullsize()
+        with open(os.path.join(HERE, "fullsize_oracle.json"), "w") as f:
+            json.dump(out, f, indent=1, sort_keys=True)
+        print("wrote", os.path.join(HERE, "fullsize_oracle.json"))
+        sys.exit(0)
     with open(os.path.join(HERE, "textbook_graphs.json"), "w") as f:
         json.dump(textbook_graphs(), f, indent=0)
     with open(os.path.join(HERE, "rmat_s14_oracle.json"), "w") as f:

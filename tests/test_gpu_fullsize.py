@@ -1,14 +1,22 @@
 """Parity at the full workload sizes, in the launch configuration bench.py
 times (tc_preprocess + tc_count on device-resident pairs).
 
-The oracle cannot count a billion-edge graph in test time, so these tests
-use what it can compute one by one -- the triangles through sampled
-vertices, counted from the definition on the host-generated copy of the
-same pairs -- plus properties that hold at any size: the per-vertex counts
-sum to three times the total, and relabelling the vertices changes neither
-the total nor (up to the relabelling) the per-vertex counts.
+The oracle cannot count a billion-edge graph in test time.  Its full
+results for these two graphs were computed once, on the host, by
+tests/golden/make_golden.py --fullsize (which calls only the oracle and the
+seeded generators) and are compared here: total, a digest of every
+per-vertex count, and the graph statistics.  The tests also use what the
+oracle computes one by one -- the triangles through sampled vertices,
+counted from the definition on the host-generated copy of the same pairs --
+and properties that hold at any size: the per-vertex counts sum to three
+times the total, and relabelling the vertices changes neither the total nor
+(up to the relabelling) the per-vertex counts.
 """
 from __future__ import annotations
+
+import hashlib
+import json
+import os
 
 import numpy as np
 import pytest
@@ -40,12 +48,31 @@ def pick_samples(s, d, n, seed):
     return np.unique(np.asarray(pick, dtype=np.int32))[:64]
 
 
-def check_full(tc, s, d, hs, hd, n, offsets):
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "fullsize_oracle.json")
+
+
+def golden(name):
+    if not os.path.exists(GOLDEN):
+        return None
+    with open(GOLDEN) as f:
+        return json.load(f).get(name)
+
+
+def check_full(tc, s, d, hs, hd, n, offsets, name):
     g = tc.preprocess(s, d, n, offsets=offsets)
     total, t = g.count(per_vertex=True)
     st = g.stats()
     g.free()
     assert int(t.sum().item()) == 3 * total
+    gold = golden(name)
+    if gold is not None:
+        # the oracle's full results on the same graph
+        assert total == gold["total"]
+        th = t.cpu().numpy().astype("<u8")
+        assert hashlib.sha256(th.tobytes()).hexdigest() == gold["per_vertex_sha256"]
+        assert st["m"] == gold["m"] and st["max_deg"] == gold["max_deg"]
+        assert st["max_outdeg"] == gold["max_outdeg"]
+        assert st["probes"] == gold["wedges_jik"] and st["probes_ijk"] == gold["wedges_ijk"]
     samples = pick_samples(s, d, n, seed=n % 9973)
     want = oracle.vertex_triangles(hs, hd, n, samples)
     got = t[torch.from_numpy(samples.astype(np.int64)).cuda()].cpu().numpy().astype(np.uint64)
@@ -76,7 +103,7 @@ def test_rmat_scale26_full_size(tc):
     hs, hd = spec.generate()
     # the device copy of the input stream is the host one
     assert np.array_equal(s[-4096:].cpu().numpy(), hs[-4096:])
-    total, st = check_full(tc, s, d, hs, hd, spec.n, offsets=64)
+    total, st = check_full(tc, s, d, hs, hd, spec.n, offsets=64, name="rmat-s26")
     assert st["offset_bytes"] == 8 and st["m"] > 10**9
 
 
@@ -85,5 +112,5 @@ def test_chung_lu_full_size(tc):
     spec = inputs.chung_lu_graph(1)
     hs, hd = spec.generate()
     s, d = torch.from_numpy(hs).cuda(), torch.from_numpy(hd).cuda()
-    total, st = check_full(tc, s, d, hs, hd, spec.n, offsets=64)
+    total, st = check_full(tc, s, d, hs, hd, spec.n, offsets=64, name="chunglu")
     assert st["max_deg"] > 10**5
