@@ -123,3 +123,29 @@ def test_components_union_matches_each_graph(tc):
     with pytest.raises(tc.TCError) as ei:
         tc.preprocess_components(bad_s, bad_d, vpre)
     assert ei.value.status == tc.TC_EINVAL
+
+
+def test_components_union_on_the_large_input_path(tc):
+    """A union of more than 2^26 pairs takes the radix-sort deduplication;
+    each component's count still equals that graph counted alone, and a
+    pair across two components is still rejected there."""
+    parts = [(5, 21, (1 << 25) + 3), (6, 21, 1 << 25)]
+    srcs, dsts, vpre, want = [], [], [0], []
+    for seed, scale, num in parts:
+        s, d = tc.generate_rmat(seed, scale, num)
+        g = tc.preprocess(s, d, 1 << scale)
+        want.append(g.count())
+        g.free()
+        srcs.append(s + vpre[-1])
+        dsts.append(d + vpre[-1])
+        vpre.append(vpre[-1] + (1 << scale))
+    s, d = torch.cat(srcs), torch.cat(dsts)
+    assert s.shape[0] > (1 << 26)
+    g = tc.preprocess_components(s, d, vpre)
+    assert tc.count_components(g).cpu().numpy().tolist() == want
+    assert g.count() == sum(want)
+    g.free()
+    s[0] = vpre[1]                       # a pair from component 0 into component 1
+    with pytest.raises(tc.TCError) as ei:
+        tc.preprocess_components(s, d, vpre)
+    assert ei.value.status == tc.TC_EINVAL
