@@ -509,10 +509,30 @@ def triangles_static(src, dst, n: int, per_vertex=None, stream=None) -> int:
     ps, dev_s = _ptr(src)
     pd, dev_d = _ptr(dst)
     assert dev_s and dev_d, "tc_triangles_static takes device pairs"
-    total = torch.zeros(1, dtype=torch.int64, device=src.device)
+    assert int(dst.shape[0]) == int(src.shape[0]), "src and dst differ in length"
+    dev = src.device
+    if per_vertex is not None:
+        assert (isinstance(per_vertex, torch.Tensor) and per_vertex.is_cuda
+                and per_vertex.device == dev), "per_vertex must be a CUDA tensor on src's device"
+        assert per_vertex.dtype in (torch.int64, torch.uint64), "per_vertex must be 64-bit"
+        assert per_vertex.is_contiguous() and per_vertex.numel() >= n, "per_vertex needs n entries"
+    # The library works on `lib_stream`; torch allocates `total` (and the
+    # caller made the inputs) on its current stream.  The library stream waits
+    # for the current one before the call, and the current one waits for the
+    # library stream before the total is read back.
+    cur = torch.cuda.current_stream(dev)
+    st = _stream_ptr(stream)
+    lib_stream = cur if st == cur.cuda_stream else (
+        stream if isinstance(stream, torch.cuda.Stream)
+        else torch.cuda.ExternalStream(st, device=dev))
+    total = torch.empty(1, dtype=torch.int64, device=dev)
+    if lib_stream is not cur:
+        lib_stream.wait_stream(cur)
     _check(load().tc_triangles_static(ps, pd, int(src.shape[0]), n, total.data_ptr(),
                                       per_vertex.data_ptr() if per_vertex is not None else None,
-                                      _stream_ptr(stream)))
+                                      st))
+    if lib_stream is not cur:
+        cur.wait_stream(lib_stream)
     return int(total.item())
 
 

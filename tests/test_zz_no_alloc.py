@@ -83,3 +83,57 @@ def test_static_entry_rejects_sizes_beyond_its_limits(tc):
     # the binding's wrapper gives the same total as the C call
     s, d = tc.generate_rmat(3, 12, 16 << 12)
     assert tc.triangles_static(s, d, 1 << 12) == allocating_path(tc, s, d, 1 << 12)[0]
+
+
+def unique_pairs(seed, scale, count):
+    """Exactly `count` distinct undirected pairs (no self-loops) on 2^scale
+    vertices, in the order an RMAT stream first produces them."""
+    n = 1 << scale
+    s, d = inputs.rmat(seed, scale, 4 * count)
+    lo, hi = np.minimum(s, d).astype(np.int64), np.maximum(s, d).astype(np.int64)
+    keep = lo != hi
+    key = (lo << 32 | hi)[keep]
+    _, first = np.unique(key, return_index=True)
+    first = np.sort(first)[:count]
+    assert first.size == count
+    return s[keep][first].copy(), d[keep][first].copy(), n
+
+
+def test_static_entry_at_its_documented_limits(tc):
+    """The worst case the scratch is sized for: TC_STATIC_MAX_VERTICES
+    vertices, TC_STATIC_MAX_PAIRS pairs that are all distinct edges (so every
+    temporary is at its largest), per-vertex counts requested."""
+    import oracle
+    hs, hd, n = unique_pairs(11, 16, tc.TC_STATIC_MAX_PAIRS)
+    assert n == tc.TC_STATIC_MAX_VERTICES and hs.size == tc.TC_STATIC_MAX_PAIRS
+    s, d = torch.from_numpy(hs).cuda(), torch.from_numpy(hd).cuda()
+    want_total, want_pv = allocating_path(tc, s, d, n)
+    got_total, got_pv = static_path(tc, s, d, n)       # asserts TC_OK, not TC_ENOMEM
+    assert got_total == want_total == oracle.count(hs, hd, n)
+    assert np.array_equal(got_pv, want_pv)
+
+
+def test_static_entry_leaves_device_memory_untouched(tc):
+    """A call on pre-allocated inputs and outputs changes the device's free
+    memory by nothing: no allocation by the library, its pool or the runtime."""
+    lib = tc.load()
+    dev = torch.cuda.current_device()
+    s, d = tc.generate_rmat(5, 14, 1 << 17)
+    n = 1 << 14
+    total = torch.zeros(1, dtype=torch.int64, device="cuda")
+    pv = torch.zeros(n, dtype=torch.int64, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    # first call: loads the kernels and looks up the scratch address
+    assert lib.tc_triangles_static(s.data_ptr(), d.data_ptr(), s.shape[0], n, total.data_ptr(),
+                                   pv.data_ptr(), st) == tc.TC_OK
+    torch.cuda.synchronize()
+    first = int(total.item())
+    tc.release_memory(dev)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    for _ in range(2):
+        assert lib.tc_triangles_static(s.data_ptr(), d.data_ptr(), s.shape[0], n,
+                                       total.data_ptr(), pv.data_ptr(), st) == tc.TC_OK
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info(dev)[0] == free0
+    assert int(total.item()) == first
