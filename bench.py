@@ -442,21 +442,37 @@ def run_ours(args, wl):
         hpv_np = hpv.numpy() if hpv is not None else None
         tc.triangles(hs_np, hd_np, n, per_vertex=wl["per_vertex"], offsets=off, out=hpv_np)
         torch.cuda.synchronize()
+        # the box's own pinned-upload rate of the same buffer, for comparison
+        up = torch.empty(num_pairs, dtype=torch.int32, device="cuda")
+        up.copy_(hs, non_blocking=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        up.copy_(hs, non_blocking=True)
+        ev1.record()
+        torch.cuda.synchronize()
+        torch_h2d_gbs = 4 * num_pairs / (ev0.elapsed_time(ev1) / 1e3) / 1e9
+        del up
         barrier()
         t0 = time.perf_counter()
+        splits = []
         for _ in range(args.steps):
             r = tc.triangles(hs_np, hd_np, n, per_vertex=wl["per_vertex"], offsets=off, out=hpv_np)
+            splits.append(tc.triangles_timing())
         torch.cuda.synchronize()
         barrier()
         e2e_s = (time.perf_counter() - t0) / args.steps
         (e2e_s,), _ = reduce_over_ranks([e2e_s], [])
         e2e_total = r[0] if isinstance(r, tuple) else r
         assert e2e_total == total, (e2e_total, total)
+        split = {k: (sum(x[k] for x in splits) / len(splits) if k != "input_pinned"
+                     else all(x[k] for x in splits)) for k in splits[0]}
         e2e = {"value": m_all / e2e_s, "unit": "edges/s", "ms_per_step": e2e_s * 1e3,
                "h2d_bytes_per_step": 8 * num_pairs,
                "d2h_bytes_per_step": 8 + (8 * n if wl["per_vertex"] else 0),
                "call": "tc_triangles (host pairs in pinned memory -> host total"
-                       + (" + per-vertex)" if wl["per_vertex"] else ")")}
+                       + (" + per-vertex)" if wl["per_vertex"] else ")"),
+               "split_ms": {k: (round(v, 3) if isinstance(v, float) else v) for k, v in split.items()},
+               "torch_pinned_h2d_gbs": torch_h2d_gbs}
         del hs, hd, hpv
 
     cpu = None

@@ -193,6 +193,26 @@ TC_API tc_status tc_triangles(const int32_t* src_host, const int32_t* dst_host, 
                        int64_t n, uint32_t flags, void* stream, uint64_t* total_host,
                        uint64_t* per_vertex_host);
 
+/* Where the time of the calling thread's last tc_triangles went.  Device
+ * phases come from CUDA events recorded on the call's stream; wall_ms is the
+ * host time of the whole call.  Not part of the paper's method.
+ *   wall_ms          host time from entry to return
+ *   h2d_ms           device time of the upload of both pair arrays
+ *   preprocess_ms    device time from the end of the upload to the end of
+ *                    tc_preprocess's work (host synchronisations included)
+ *   count_ms         device time of the count (and per-vertex gather)
+ *   d2h_ms           device time of the copies of the results to the host
+ *   h2d_issue_ms     host time spent issuing the upload (as long as the copy
+ *                    itself when the pairs are pageable host memory)
+ *   input_pinned     1 if both pair arrays are page-locked host memory
+ * TC_EINVAL on NULL out or when this thread made no successful call. */
+typedef struct {
+    double wall_ms, h2d_ms, preprocess_ms, count_ms, d2h_ms, h2d_issue_ms;
+    int32_t input_pinned;
+    int32_t pad;
+} tc_triangles_timing;
+TC_API tc_status tc_triangles_get_timing(tc_triangles_timing* out);
+
 /* Work done by the last tc_count on a graph, read from device counters:
  * index 0 is the warp kernel (pivots with |U_j| <= small_max_outdeg), index 1
  * the CTA kernel.  probes = entries of the rows U_i read and looked up. */
@@ -223,6 +243,18 @@ TC_API void tc_graph_free(tc_graph* g);
  * method.  TC_EINVAL for a device index above the library's limit (64);
  * TC_ECUDA. */
 TC_API tc_status tc_release_memory(int device);
+
+/* Device memory of the library's own pool on `device` (not part of the
+ * paper's method): bytes reserved from the device, bytes in live
+ * allocations, and the high-water marks of both since the pool was created
+ * or since the last call with reset_high != 0 (which zeroes them after
+ * reading).  Allocations through a caller's tc_allocator are not seen.
+ * TC_EINVAL for NULL out or a device outside [0, 64); TC_ECUDA. */
+typedef struct {
+    int64_t reserved, reserved_high;
+    int64_t used, used_high;
+} tc_memory_stats;
+TC_API tc_status tc_memory_get_stats(int device, int32_t reset_high, tc_memory_stats* out);
 
 /* Self-test of the device's bounded waits (not part of the paper's method).
  * One warp waits, with the wait the radix sort's look-back uses, for a
@@ -306,6 +338,10 @@ TC_API tc_status tc_count_batch(const tc_graph* const* graphs, int32_t num, cons
  * tc_server_submit_rmat: queue one request; *ticket (may be NULL) gets its
  *   id.  TC_EINVAL for a bad spec; TC_EBUSY if the request alone exceeds the
  *   budget (it is dropped).
+ * tc_server_submit_rmat_many: queue count requests at once, in order, under
+ *   one lock (a worker that wakes sees all of them); t_arrival[k] and
+ *   tickets[k] (tickets may be NULL) as above.  All or nothing: if any spec
+ *   is bad (TC_EINVAL) or over the budget (TC_EBUSY), none is queued.
  * tc_server_poll: move up to max finished results to out (waiting up to
  *   wait_ms for the first); *count gets how many.
  * tc_server_drain: wait until every submitted request is done; TC_ETIMEOUT
@@ -338,16 +374,23 @@ typedef struct {
     double t_arrival, t_admit, t_done;
     int32_t status;        /* TC_OK, or the error of the request's tick */
     int32_t tick_requests; /* requests counted in the same tick */
+    int64_t tick_pairs;    /* pairs of all requests of that tick */
+    double t_dev_start, t_dev_end;   /* device time span of the tick (seconds
+                                        from server creation; -1 if unknown) */
 } tc_server_result;
 typedef struct {
     int64_t submitted, completed, failed, pending, ticks;
     int64_t bytes_in_flight, peak_bytes_in_flight, busy_workers;
+    double device_busy_s;     /* device time covered by at least one tick's span */
+    double device_overlap_s;  /* device time covered by two or more ticks' spans */
 } tc_server_stats;
 
 TC_API tc_status tc_server_create(const tc_server_config* cfg, tc_server** out);
 TC_API double tc_server_now(const tc_server* s);
 TC_API tc_status tc_server_submit_rmat(tc_server* s, const tc_rmat_spec* spec, double t_arrival,
                                        int64_t* ticket);
+TC_API tc_status tc_server_submit_rmat_many(tc_server* s, const tc_rmat_spec* specs, int32_t count,
+                                            const double* t_arrival, int64_t* tickets);
 TC_API tc_status tc_server_poll(tc_server* s, tc_server_result* out, int32_t max, int32_t* count,
                                 int32_t wait_ms);
 TC_API tc_status tc_server_drain(tc_server* s, int32_t timeout_ms);

@@ -1,4 +1,5 @@
 // C ABI entry points: argument checks, error capture, allocation, ownership.
+#include <chrono>
 #include <cstdarg>
 #include <cstring>
 #include <mutex>
@@ -114,6 +115,34 @@ void tuning_resolve(const tc_tuning* in, tc_tuning* out) {
 bool tuning_equal(const tc_tuning& a, const tc_tuning& b) {
     return std::memcmp(&a, &b, sizeof(tc_tuning)) == 0;
 }
+
+// Five timing events, destroyed with the scope.
+struct Events {
+    cudaEvent_t e[5] = {};
+    Events() {
+        for (auto& x : e) TC_CUDA(cudaEventCreate(&x));
+    }
+    ~Events() {
+        for (auto& x : e)
+            if (x) cudaEventDestroy(x);
+    }
+    double ms(int a, int b) const {
+        float v = 0.f;
+        return cudaEventElapsedTime(&v, e[a], e[b]) == cudaSuccess ? (double)v : -1.0;
+    }
+};
+
+bool is_pinned(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+static thread_local tc_triangles_timing g_last_timing{};
+static thread_local bool g_have_timing = false;
 
 static void graph_release(tc_graph* g) {
     if (!g) return;
@@ -273,34 +302,67 @@ tc_status tc_triangles(const int32_t* src_host, const int32_t* dst_host, int64_t
     TC_API_BEGIN
     if (!total_host) TC_FAIL(TC_EINVAL, "tc_triangles: total_host is NULL");
     if (flags & TC_INPUT_ON_DEVICE) TC_FAIL(TC_EINVAL, "tc_triangles: takes host inputs");
-    tc_graph* g = nullptr;
-    tc_status s = tc_preprocess(src_host, dst_host, num_pairs, n, flags, nullptr, stream, &g);
-    if (s != TC_OK) return s;
+    if (num_pairs < 0) TC_FAIL(TC_EINVAL, "tc_triangles: num_pairs < 0");
+    if (n < 0 || n >= (int64_t)0x7fffffff) TC_FAIL(TC_EINVAL, "tc_triangles: n outside [0, 2^31-1)");
+    if (num_pairs > 0 && (!src_host || !dst_host)) TC_FAIL(TC_EINVAL, "tc_triangles: src or dst is NULL");
+    if (num_pairs > (int64_t)0x7fffffff) TC_FAIL(TC_EINVAL, "tc_triangles: num_pairs >= 2^31");
+    if ((flags & TC_OFFSETS_32) && (flags & TC_OFFSETS_64))
+        TC_FAIL(TC_EINVAL, "tc_triangles: both offset widths requested");
+    const auto wall0 = std::chrono::steady_clock::now();
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Events ev;
+    tc_triangles_timing tm{};
+    tm.input_pinned = num_pairs > 0 && is_pinned(src_host) && is_pinned(dst_host);
+    tc_graph* g = new tc_graph();
+    g->n = n;
+    g->num_pairs = num_pairs;
+    g->bits = std::max(1, ceil_log2_u64((uint64_t)std::max<int64_t>(n, 1)));
+    g->alloc.stream = st;
+    g->stats.n = n;
+    g->stats.num_pairs = num_pairs;
+    g->ev_uploaded = ev.e[1];
+    uint64_t* pv = nullptr;
     try {
+        TC_CUDA(cudaEventRecord(ev.e[0], st));
+        preprocess(g, src_host, dst_host, num_pairs, flags, st);
+        TC_CUDA(cudaEventRecord(ev.e[2], st));
         tc_tuning t;
         tuning_resolve(nullptr, &t);
-        uint64_t* pv = nullptr;
         if (per_vertex_host && n > 0) pv = static_cast<uint64_t*>(g->alloc.get(sizeof(uint64_t) * n));
-        try {
-            count(g, t, nullptr, pv, st);
-            unsigned long long v = 0;
-            TC_CUDA(cudaMemcpyAsync(&v, g->counters + CTR_TOTAL, sizeof(v), cudaMemcpyDeviceToHost, st));
-            if (pv)
-                TC_CUDA(cudaMemcpyAsync(per_vertex_host, pv, sizeof(uint64_t) * n,
-                                        cudaMemcpyDeviceToHost, st));
-            TC_CUDA(cudaStreamSynchronize(st));
-            *total_host = v;
-        } catch (...) {
-            if (pv) g->alloc.put(pv, sizeof(uint64_t) * n);
-            throw;
-        }
-        if (pv) g->alloc.put(pv, sizeof(uint64_t) * n);
+        count(g, t, nullptr, pv, st);
+        TC_CUDA(cudaEventRecord(ev.e[3], st));
+        unsigned long long v = 0;
+        TC_CUDA(cudaMemcpyAsync(&v, g->counters + CTR_TOTAL, sizeof(v), cudaMemcpyDeviceToHost, st));
+        if (pv)
+            TC_CUDA(cudaMemcpyAsync(per_vertex_host, pv, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaEventRecord(ev.e[4], st));
+        TC_CUDA(cudaStreamSynchronize(st));
+        *total_host = v;
     } catch (...) {
+        if (pv) g->alloc.put(pv, sizeof(uint64_t) * n);
+        g->ev_uploaded = nullptr;
         graph_release(g);
         throw;
     }
+    if (pv) g->alloc.put(pv, sizeof(uint64_t) * n);
+    tm.h2d_issue_ms = g->upload_issue_ms;
+    g->ev_uploaded = nullptr;
     graph_release(g);
+    tm.h2d_ms = ev.ms(0, 1);
+    tm.preprocess_ms = ev.ms(1, 2);
+    tm.count_ms = ev.ms(2, 3);
+    tm.d2h_ms = ev.ms(3, 4);
+    tm.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
+    g_last_timing = tm;
+    g_have_timing = true;
+    TC_API_END
+}
+
+tc_status tc_triangles_get_timing(tc_triangles_timing* out) {
+    TC_API_BEGIN
+    if (!out) TC_FAIL(TC_EINVAL, "tc_triangles_get_timing: out is NULL");
+    if (!g_have_timing) TC_FAIL(TC_EINVAL, "tc_triangles_get_timing: no tc_triangles call on this thread yet");
+    *out = g_last_timing;
     TC_API_END
 }
 
@@ -342,6 +404,28 @@ tc_status tc_selftest_wait_timeout(int64_t spin_limit, void* stream) {
     if (selftest_wait_timeout((long)spin_limit, al, al.stream))
         TC_FAIL(TC_ETIMEOUT, "tc_selftest_wait_timeout: the bounded wait ran out and reported it");
     TC_FAIL(TC_ECUDA, "tc_selftest_wait_timeout: the wait ended without its word being published");
+    TC_API_END
+}
+
+tc_status tc_memory_get_stats(int device, int32_t reset_high, tc_memory_stats* out) {
+    TC_API_BEGIN
+    if (!out || device < 0 || device >= kMaxDevices)
+        TC_FAIL(TC_EINVAL, "tc_memory_get_stats: NULL out or device %d out of range", device);
+    cudaMemPool_t pool = library_pool(device);
+    uint64_t v[4] = {0, 0, 0, 0};
+    TC_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &v[0]));
+    TC_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemHigh, &v[1]));
+    TC_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v[2]));
+    TC_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &v[3]));
+    out->reserved = (int64_t)v[0];
+    out->reserved_high = (int64_t)v[1];
+    out->used = (int64_t)v[2];
+    out->used_high = (int64_t)v[3];
+    if (reset_high) {
+        uint64_t zero = 0;
+        TC_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReservedMemHigh, &zero));
+        TC_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+    }
     TC_API_END
 }
 

@@ -170,6 +170,12 @@ struct tc_graph {
     unsigned* tlow = nullptr;   // 32-bit per-task shares (per-vertex counts), n, on demand
     size_t tlow_bytes = 0;
 
+    // instrumentation of a host-input preprocessing (set by tc_triangles):
+    // an event recorded on the stream once the pairs are uploaded, and the
+    // host time spent issuing the upload (long when the source is pageable)
+    cudaEvent_t ev_uploaded = nullptr;
+    double upload_issue_ms = 0.0;
+
     int64_t n_tasks = 0, n_small = 0, n_large = 0;
     void* units_mem = nullptr;      // small units, then large units
     size_t units_bytes = 0;

@@ -16,6 +16,7 @@
 //
 // b = ceil(log2 n) bits per id, so keys use 2b <= 62 bits.
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 
 #include "common.cuh"
@@ -381,11 +382,15 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
     if (!(flags & TC_INPUT_ON_DEVICE) && P > 0) {
         hsrc = Buf<int32_t>(al, (size_t)P);
         hdst = Buf<int32_t>(al, (size_t)P);
+        const auto t0 = std::chrono::steady_clock::now();
         TC_CUDA(cudaMemcpyAsync(hsrc.get(), src_in, sizeof(int32_t) * P, cudaMemcpyHostToDevice, st));
         TC_CUDA(cudaMemcpyAsync(hdst.get(), dst_in, sizeof(int32_t) * P, cudaMemcpyHostToDevice, st));
+        g->upload_issue_ms =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         src = hsrc.get();
         dst = hdst.get();
     }
+    if (g->ev_uploaded) TC_CUDA(cudaEventRecord(g->ev_uploaded, st));
 
     Buf<int> scal(al, 8);   // [0] err, [1] max degree, [2] max out-degree
     TC_CUDA(cudaMemsetAsync(scal.get(), 0, 8 * sizeof(int), st));

@@ -43,6 +43,8 @@ struct tc_server {
     tc_server_config cfg{};
     int device = 0;
     std::chrono::steady_clock::time_point t0;
+    cudaEvent_t ev_ref = nullptr;        // device time origin of the tick spans
+    std::vector<std::pair<double, double>> spans;   // per tick: device start, end (s)
     std::mutex mu;
     std::condition_variable cv;
     std::deque<Pending> pending;
@@ -64,8 +66,10 @@ struct tc_server {
 namespace tc {
 namespace {
 
-// Runs one tick on stream st; fills totals (one per request).
-void run_tick(const std::vector<Pending>& reqs, std::vector<uint64_t>& totals, cudaStream_t st) {
+// Runs one tick on stream st; fills totals (one per request).  e0 and e1 are
+// recorded on st before the tick's first device operation and after its last.
+void run_tick(const std::vector<Pending>& reqs, std::vector<uint64_t>& totals, cudaStream_t st,
+              cudaEvent_t e0, cudaEvent_t e1) {
     const int nreq = (int)reqs.size();
     std::vector<int64_t> ppre(nreq + 1, 0), vpre(nreq + 1, 0);
     std::vector<RmatJob> jobs(nreq);
@@ -82,6 +86,7 @@ void run_tick(const std::vector<Pending>& reqs, std::vector<uint64_t>& totals, c
     Buf<int64_t> dppre(al, (size_t)nreq + 1);
     Buf<int32_t> src(al, (size_t)std::max<int64_t>(P, 1)), dst(al, (size_t)std::max<int64_t>(P, 1));
     Buf<uint64_t> dtot(al, (size_t)nreq);
+    TC_CUDA(cudaEventRecord(e0, st));
     TC_CUDA(cudaMemcpyAsync(djobs.get(), jobs.data(), sizeof(RmatJob) * nreq, cudaMemcpyHostToDevice, st));
     TC_CUDA(cudaMemcpyAsync(dppre.get(), ppre.data(), sizeof(int64_t) * (nreq + 1), cudaMemcpyHostToDevice, st));
     generate_rmat_multi(djobs.get(), dppre.get(), nreq, P, src.get(), dst.get(), st);
@@ -99,6 +104,7 @@ void run_tick(const std::vector<Pending>& reqs, std::vector<uint64_t>& totals, c
         count_components(g, t, dtot.get(), st);
         totals.assign(nreq, 0);
         TC_CUDA(cudaMemcpyAsync(totals.data(), dtot.get(), sizeof(uint64_t) * nreq, cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaEventRecord(e1, st));
         TC_CUDA(cudaStreamSynchronize(st));
     } catch (...) {
         if (g->units_mem) g->alloc.put(g->units_mem, g->units_bytes);
@@ -114,7 +120,9 @@ void run_tick(const std::vector<Pending>& reqs, std::vector<uint64_t>& totals, c
 void worker_loop(tc_server* S) {
     cudaSetDevice(S->device);
     cudaStream_t st = nullptr;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         std::lock_guard<std::mutex> lk(S->mu);
         S->first_error = TC_ECUDA;
         return;
@@ -150,14 +158,23 @@ void worker_loop(tc_server* S) {
         const double t_admit = S->now();
         std::vector<uint64_t> totals;
         tc_status status = TC_OK;
+        double d0 = -1.0, d1 = -1.0;
         try {
-            run_tick(tick, totals, st);
+            run_tick(tick, totals, st, e0, e1);
+            float a = 0.f, b = 0.f;
+            if (cudaEventElapsedTime(&a, S->ev_ref, e0) == cudaSuccess &&
+                cudaEventElapsedTime(&b, S->ev_ref, e1) == cudaSuccess) {
+                d0 = a * 1e-3;
+                d1 = b * 1e-3;
+            }
         } catch (const Error& e) {
             status = e.status;
         } catch (...) {
             status = TC_ECUDA;
         }
         const double t_done = S->now();
+        int64_t tick_pairs = 0;
+        for (const Pending& p : tick) tick_pairs += p.spec.num_pairs;
         {
             std::lock_guard<std::mutex> lk(S->mu);
             for (size_t r = 0; r < tick.size(); ++r) {
@@ -169,8 +186,12 @@ void worker_loop(tc_server* S) {
                 res.t_done = t_done;
                 res.status = status;
                 res.tick_requests = (int32_t)tick.size();
+                res.tick_pairs = tick_pairs;
+                res.t_dev_start = d0;
+                res.t_dev_end = d1;
                 S->done.push_back(res);
             }
+            if (d0 >= 0.0) S->spans.emplace_back(d0, d1);
             S->completed += (int64_t)tick.size();
             if (status != TC_OK) {
                 S->failed += (int64_t)tick.size();
@@ -184,6 +205,29 @@ void worker_loop(tc_server* S) {
     }
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+}
+
+// Device time covered by at least one tick and by at least two, from the
+// ticks' [start, end] spans.
+void span_cover(std::vector<std::pair<double, double>> v, double& busy, double& overlap) {
+    busy = overlap = 0.0;
+    std::vector<std::pair<double, int>> ev;
+    ev.reserve(2 * v.size());
+    for (auto& p : v) {
+        ev.emplace_back(p.first, +1);
+        ev.emplace_back(p.second, -1);
+    }
+    std::sort(ev.begin(), ev.end());
+    int depth = 0;
+    double last = 0.0;
+    for (auto& e : ev) {
+        if (depth >= 1) busy += e.first - last;
+        if (depth >= 2) overlap += e.first - last;
+        depth += e.second;
+        last = e.first;
+    }
 }
 
 }  // namespace
@@ -215,6 +259,22 @@ tc_status tc_server_create(const tc_server_config* cfg, tc_server** out) {
     } else {
         S->device = S->cfg.device;
     }
+    {
+        int prev = 0;
+        cudaGetDevice(&prev);
+        bool ok = cudaSetDevice(S->device) == cudaSuccess &&
+                  cudaEventCreate(&S->ev_ref) == cudaSuccess &&
+                  cudaEventRecord(S->ev_ref, nullptr) == cudaSuccess &&
+                  cudaEventSynchronize(S->ev_ref) == cudaSuccess;
+        cudaSetDevice(prev);
+        if (!ok) {
+            const int dev = S->device;
+            if (S->ev_ref) cudaEventDestroy(S->ev_ref);
+            delete S;
+            set_error("tc_server_create: cannot set up device %d", dev);
+            return TC_ECUDA;
+        }
+    }
     S->t0 = std::chrono::steady_clock::now();
     for (int w = 0; w < S->cfg.workers; ++w) S->workers.emplace_back(worker_loop, S);
     *out = S;
@@ -223,36 +283,58 @@ tc_status tc_server_create(const tc_server_config* cfg, tc_server** out) {
 
 double tc_server_now(const tc_server* s) { return s ? s->now() : 0.0; }
 
+}  // extern "C"
+
+namespace {
+
+bool spec_ok(const tc_rmat_spec& s) {
+    return s.scale >= 1 && s.scale <= 31 && s.n >= 1 && s.n <= (1ll << s.scale) &&
+           s.num_pairs >= 0 && s.num_pairs <= (int64_t)0x7fffffff && s.t1 <= s.t2 && s.t2 <= s.t3;
+}
+
+}  // namespace
+
+extern "C" {
+
 tc_status tc_server_submit_rmat(tc_server* s, const tc_rmat_spec* spec, double t_arrival,
                                 int64_t* ticket) {
+    return tc_server_submit_rmat_many(s, spec, 1, &t_arrival, ticket);
+}
+
+tc_status tc_server_submit_rmat_many(tc_server* s, const tc_rmat_spec* specs, int32_t count,
+                                     const double* t_arrival, int64_t* tickets) {
     clear_error();
-    if (!s || !spec) {
-        set_error("tc_server_submit_rmat: NULL argument");
+    if (!s || count < 0 || (count > 0 && (!specs || !t_arrival))) {
+        set_error("tc_server_submit_rmat: NULL argument or negative count");
         return TC_EINVAL;
     }
-    if (spec->scale < 1 || spec->scale > 31 || spec->n < 1 || spec->n > (1ll << spec->scale) ||
-        spec->num_pairs < 0 || spec->num_pairs > (int64_t)0x7fffffff ||
-        !(spec->t1 <= spec->t2 && spec->t2 <= spec->t3)) {
-        set_error("tc_server_submit_rmat: bad request spec");
-        return TC_EINVAL;
-    }
-    Pending p;
-    p.spec = *spec;
-    p.t_arrival = t_arrival;
-    p.bytes = footprint(*spec);
+    for (int32_t k = 0; k < count; ++k)
+        if (!spec_ok(specs[k])) {
+            set_error("tc_server_submit_rmat: bad request spec (request %d)", k);
+            return TC_EINVAL;
+        }
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        if (p.bytes > s->cfg.hbm_budget_bytes) {
-            set_error("tc_server_submit_rmat: request needs %lld bytes, over the %lld-byte budget",
-                      (long long)p.bytes, (long long)s->cfg.hbm_budget_bytes);
-            return TC_EBUSY;
+        for (int32_t k = 0; k < count; ++k) {
+            const int64_t bytes = footprint(specs[k]);
+            if (bytes > s->cfg.hbm_budget_bytes) {
+                set_error("tc_server_submit_rmat: request %d needs %lld bytes, over the %lld-byte "
+                          "budget", k, (long long)bytes, (long long)s->cfg.hbm_budget_bytes);
+                return TC_EBUSY;
+            }
         }
-        p.ticket = s->next_ticket++;
-        s->pending.push_back(p);
-        s->submitted += 1;
+        for (int32_t k = 0; k < count; ++k) {
+            Pending p;
+            p.spec = specs[k];
+            p.t_arrival = t_arrival[k];
+            p.bytes = footprint(specs[k]);
+            p.ticket = s->next_ticket++;
+            s->pending.push_back(p);
+            s->submitted += 1;
+            if (tickets) tickets[k] = p.ticket;
+        }
     }
-    s->cv.notify_one();
-    if (ticket) *ticket = p.ticket;
+    s->cv.notify_all();
     return TC_OK;
 }
 
@@ -305,6 +387,7 @@ tc_status tc_server_get_stats(tc_server* s, tc_server_stats* out) {
     out->bytes_in_flight = s->bytes_in_flight;
     out->peak_bytes_in_flight = s->peak_bytes;
     out->busy_workers = s->busy_workers;
+    span_cover(s->spans, out->device_busy_s, out->device_overlap_s);
     return TC_OK;
 }
 
@@ -316,6 +399,7 @@ void tc_server_free(tc_server* s) {
     }
     s->cv.notify_all();
     for (auto& t : s->workers) t.join();
+    if (s->ev_ref) cudaEventDestroy(s->ev_ref);
     delete s;
 }
 

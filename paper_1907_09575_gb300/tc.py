@@ -69,7 +69,8 @@ EXPORTS = ("tc_preprocess", "tc_count", "tc_triangles", "tc_graph_get_stats", "t
            "tc_batch_free", "tc_count_batch", "tc_preprocess_components", "tc_count_components",
            "tc_server_create", "tc_server_now", "tc_server_submit_rmat", "tc_server_poll",
            "tc_server_drain", "tc_server_get_stats", "tc_server_free", "tc_release_memory",
-           "tc_selftest_wait_timeout")
+           "tc_selftest_wait_timeout", "tc_server_submit_rmat_many", "tc_memory_get_stats",
+           "tc_triangles_get_timing")
 
 TC_STATIC_MAX_PAIRS = 262144
 TC_STATIC_MAX_VERTICES = 65536
@@ -97,13 +98,25 @@ class ServerResult(ctypes.Structure):
     _fields_ = [("ticket", ctypes.c_int64), ("triangles", ctypes.c_uint64),
                 ("t_arrival", ctypes.c_double), ("t_admit", ctypes.c_double),
                 ("t_done", ctypes.c_double), ("status", ctypes.c_int32),
-                ("tick_requests", ctypes.c_int32)]
+                ("tick_requests", ctypes.c_int32), ("tick_pairs", ctypes.c_int64),
+                ("t_dev_start", ctypes.c_double), ("t_dev_end", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "completed", "failed", "pending", "ticks",
                                                "bytes_in_flight", "peak_bytes_in_flight",
-                                               "busy_workers")]
+                                               "busy_workers")] + \
+               [("device_busy_s", ctypes.c_double), ("device_overlap_s", ctypes.c_double)]
+
+
+class MemoryStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("reserved", "reserved_high", "used", "used_high")]
+
+
+class TrianglesTiming(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_double) for f in ("wall_ms", "h2d_ms", "preprocess_ms", "count_ms",
+                                                "d2h_ms", "h2d_issue_ms")] + \
+               [("input_pinned", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class KernelTime(ctypes.Structure):
@@ -151,6 +164,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tc_server_submit_rmat.argtypes = [vp, ctypes.POINTER(RmatSpec), ctypes.c_double,
                                           ctypes.POINTER(i64)]
     lib.tc_server_submit_rmat.restype = st
+    lib.tc_server_submit_rmat_many.argtypes = [vp, ctypes.POINTER(RmatSpec), i32,
+                                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+    lib.tc_server_submit_rmat_many.restype = st
+    lib.tc_memory_get_stats.argtypes = [ctypes.c_int, i32, ctypes.POINTER(MemoryStats)]
+    lib.tc_memory_get_stats.restype = st
+    lib.tc_triangles_get_timing.argtypes = [ctypes.POINTER(TrianglesTiming)]
+    lib.tc_triangles_get_timing.restype = st
     lib.tc_server_poll.argtypes = [vp, ctypes.POINTER(ServerResult), i32, ctypes.POINTER(i32), i32]
     lib.tc_server_poll.restype = st
     lib.tc_server_drain.argtypes = [vp, i32]
@@ -244,6 +264,14 @@ def release_memory(device: int = -1) -> None:
     """tc_release_memory: give back the device memory the library's pool keeps
     for reuse (device -1: every device)."""
     _check(load().tc_release_memory(device))
+
+
+def memory_stats(device: int = 0, reset_high: bool = False) -> dict:
+    """tc_memory_get_stats: bytes reserved and in use in the library's pool of
+    `device`, with their high-water marks (zeroed after reading if reset_high)."""
+    m = MemoryStats()
+    _check(load().tc_memory_get_stats(device, 1 if reset_high else 0, ctypes.byref(m)))
+    return {f: int(getattr(m, f)) for f, _ in MemoryStats._fields_}
 
 
 def tuning_default() -> Tuning:
@@ -379,8 +407,26 @@ class Server:
                                             ctypes.byref(t)))
         return int(t.value)
 
+    def submit_many(self, specs, thresholds: Optional[tuple] = None,
+                    t_arrival: Optional[list] = None) -> list:
+        """Queue several requests at once (tc_server_submit_rmat_many): specs
+        are (seed, scale, n, num_pairs) tuples; returns their tickets."""
+        if thresholds is None:
+            from .inputs import rmat_thresholds
+            thresholds = rmat_thresholds()
+        k = len(specs)
+        arr = (RmatSpec * max(k, 1))()
+        for i, (seed, scale, n, num_pairs) in enumerate(specs):
+            arr[i] = RmatSpec(seed & (2**64 - 1), scale, 0, n, num_pairs, *thresholds, 0)
+        now = self.now()
+        ta = (ctypes.c_double * max(k, 1))(*(t_arrival if t_arrival is not None else [now] * k))
+        tk = (ctypes.c_int64 * max(k, 1))()
+        _check(load().tc_server_submit_rmat_many(self._h, arr, k, ta, tk))
+        return [int(tk[i]) for i in range(k)]
+
     def poll(self, wait_ms: int = 0) -> list:
-        """Finished results as dicts (ticket, triangles, times, status, tick_requests)."""
+        """Finished results as dicts (ticket, triangles, times, status, tick
+        size, the tick's device span)."""
         cnt = ctypes.c_int32(0)
         out = []
         while True:
@@ -390,7 +436,9 @@ class Server:
                 r = self._buf[i]
                 out.append({"ticket": int(r.ticket), "triangles": int(r.triangles),
                             "t_arrival": r.t_arrival, "t_admit": r.t_admit, "t_done": r.t_done,
-                            "status": int(r.status), "tick_requests": int(r.tick_requests)})
+                            "status": int(r.status), "tick_requests": int(r.tick_requests),
+                            "tick_pairs": int(r.tick_pairs), "t_dev_start": r.t_dev_start,
+                            "t_dev_end": r.t_dev_end})
             if cnt.value < len(self._buf):
                 return out
 
@@ -497,6 +545,15 @@ def triangles(src: np.ndarray, dst: np.ndarray, n: int, per_vertex: bool = False
     if per_vertex:
         return int(total.value), pv[:n]
     return int(total.value)
+
+
+def triangles_timing() -> dict:
+    """tc_triangles_get_timing: the phase split of this thread's last
+    tc_triangles call (device phases from CUDA events, wall time on the host)."""
+    t = TrianglesTiming()
+    _check(load().tc_triangles_get_timing(ctypes.byref(t)))
+    return {f: (bool(t.input_pinned) if f == "input_pinned" else float(getattr(t, f)))
+            for f, _ in TrianglesTiming._fields_ if f != "pad"}
 
 
 def triangles_static(src, dst, n: int, per_vertex=None, stream=None) -> int:

@@ -11,9 +11,17 @@
   workloads, RMAT scale 26 (edge factor 16, seed 1) and the Chung-Lu graph
   (5e7 vertices, seed 1): total, a digest of the per-vertex counts, the
   graph statistics.
+* ``batch4096_oracle.json`` (``--batch``, a few minutes on all host cores):
+  the oracle's total for every one of the 4096 graphs of the batched
+  workload (seed 1), with each graph's size and a digest of its pairs.
+* ``serve_top_oracle.json`` (``--serve-top``): the oracle's totals for the
+  first 32 requests of the served stream (seed 1) whose pair count lies in
+  the top band, 2^20..2^22 pairs; together they hold more than 2^26 pairs,
+  so a tick carrying all of them takes the large-input deduplication path.
 Only ``oracle/`` and the seeded input generators are called.
 
-Run from the repository root:  python tests/golden/make_golden.py [--fullsize]
+Run from the repository root:
+  python tests/golden/make_golden.py [--fullsize | --batch | --serve-top]
 """
 from __future__ import annotations
 
@@ -146,7 +154,72 @@ def fullsize():
     return res
 
 
+def _pairs_digest(src, dst) -> str:
+    return hashlib.sha256(src.astype("<i4").tobytes() + dst.astype("<i4").tobytes()).hexdigest()
+
+
+def _batch_one(args):
+    seed, g = args
+    import oracle
+    from paper_1907_09575_gb300 import inputs
+    spec = inputs.batch_member(seed, g)
+    src, dst = spec.generate()
+    total, st = oracle.count(src, dst, spec.n, stats=True)
+    return g, spec.n, int(src.shape[0]), st["m"], total, _pairs_digest(src, dst)[:16]
+
+
+def _pool():
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    return ProcessPoolExecutor(max_workers=os.cpu_count() or 1, mp_context=mp.get_context("spawn"))
+
+
+def batch4096(seed=1, graphs=4096):
+    """The oracle over every graph of the batch (one graph per task)."""
+    rows = [None] * graphs
+    with _pool() as ex:
+        for r in ex.map(_batch_one, [(seed, g) for g in range(graphs)], chunksize=8):
+            rows[r[0]] = r
+    return dict(seed=seed, graphs=graphs,
+                n=[r[1] for r in rows], num_pairs=[r[2] for r in rows], m=[r[3] for r in rows],
+                total=[r[4] for r in rows], pairs_sha256_16=[r[5] for r in rows],
+                source="oracle.count on inputs.batch_member(seed, g), g = 0..graphs-1")
+
+
+def _serve_one(args):
+    seed, r = args
+    import oracle
+    from paper_1907_09575_gb300 import inputs
+    spec = inputs.serve_request(seed, r)
+    src, dst = spec.generate()
+    total, st = oracle.count(src, dst, spec.n, stats=True)
+    return dict(r=r, seed=spec.seed, scale=spec.scale, n=spec.n, num_pairs=spec.num_pairs,
+                m=st["m"], total=total, pairs_sha256_16=_pairs_digest(src, dst)[:16])
+
+
+def serve_top(seed=1, count=32, lo=1 << 20):
+    """The first `count` requests of the served stream with >= lo pairs."""
+    from paper_1907_09575_gb300 import inputs
+    picks, r = [], 0
+    while len(picks) < count:
+        if inputs.serve_request(seed, r).num_pairs >= lo:
+            picks.append(r)
+        r += 1
+    with _pool() as ex:
+        reqs = list(ex.map(_serve_one, [(seed, r) for r in picks]))
+    return dict(seed=seed, band=[lo, 1 << 22], requests=reqs,
+                source="oracle.count on inputs.serve_request(seed, r) for the listed r")
+
+
 if __name__ == "__main__":
+    for flag, fn, name in (("--batch", batch4096, "batch4096_oracle.json"),
+                           ("--serve-top", serve_top, "serve_top_oracle.json")):
+        if flag in sys.argv:
+            out = fn()
+            with open(os.path.join(HERE, name), "w") as f:
+                json.dump(out, f, separators=(",", ":"))
+            print("wrote", os.path.join(HERE, name))
+            sys.exit(0)
     if "--fullsize" in sys.argv:
         out = fullsize()
         with open(os.path.join(HERE, "fullsize_oracle.json"), "w") as f:

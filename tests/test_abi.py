@@ -72,6 +72,10 @@ int main(void) {
   printf("%zu %zu %zu\n", sizeof(tc_tuning), sizeof(tc_graph_stats), sizeof(tc_allocator));
   printf("%zu %zu %zu\n", offsetof(tc_graph_stats, probes), offsetof(tc_graph_stats, device_bytes),
          offsetof(tc_tuning, slice_max));
+  printf("%zu %zu %zu %zu\n", sizeof(tc_server_result), offsetof(tc_server_result, tick_pairs),
+         sizeof(tc_server_stats), offsetof(tc_server_stats, device_overlap_s));
+  printf("%zu %zu %zu %zu\n", sizeof(tc_memory_stats), sizeof(tc_rmat_spec), sizeof(tc_server_config),
+         sizeof(tc_triangles_timing));
   return 0;
 }
 '''
@@ -80,12 +84,19 @@ int main(void) {
         exe = os.path.join(d, "p")
         open(c, "w").write(src)
         subprocess.run(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe], check=True)
-        a, b = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
+        a, b, c, e = subprocess.run([exe], capture_output=True, text=True,
+                                    check=True).stdout.split("\n")[:4]
     sizes = [int(x) for x in a.split()]
     offs = [int(x) for x in b.split()]
     assert sizes == [ctypes.sizeof(tc.Tuning), ctypes.sizeof(tc.GraphStats), ctypes.sizeof(tc.Allocator)]
     assert offs == [tc.GraphStats.probes.offset, tc.GraphStats.device_bytes.offset,
                     tc.Tuning.slice_max.offset]
+    assert [int(x) for x in c.split()] == [ctypes.sizeof(tc.ServerResult), tc.ServerResult.tick_pairs.offset,
+                                          ctypes.sizeof(tc.ServerStats),
+                                          tc.ServerStats.device_overlap_s.offset]
+    assert [int(x) for x in e.split()] == [ctypes.sizeof(tc.MemoryStats), ctypes.sizeof(tc.RmatSpec),
+                                          ctypes.sizeof(tc.ServerConfig),
+                                          ctypes.sizeof(tc.TrianglesTiming)]
 
 
 def test_missing_library_fails_loudly(tmp_path):

@@ -38,3 +38,51 @@ def test_rmat_scale26_pairs_are_the_stored_ones(gold):
     h.update(src.astype("<i4", copy=False).tobytes())
     h.update(dst.astype("<i4", copy=False).tobytes())
     assert h.hexdigest() == g["pairs_sha256"]
+
+
+def _digest16(src, dst):
+    return hashlib.sha256(src.astype("<i4").tobytes() + dst.astype("<i4").tobytes()).hexdigest()[:16]
+
+
+def test_stored_batch_results_belong_to_the_batch():
+    """tests/golden/batch4096_oracle.json (make_golden.py --batch): one entry
+    per graph of the batch, sizes equal to the generator's, pairs digests
+    equal for a sample of graphs, and totals within what m edges allow."""
+    import math
+    with open(os.path.join(os.path.dirname(GOLDEN), "batch4096_oracle.json")) as f:
+        b = json.load(f)
+    num = b["graphs"]
+    assert num == 4096
+    for key in ("n", "num_pairs", "m", "total", "pairs_sha256_16"):
+        assert len(b[key]) == num, key
+    for g in range(num):
+        assert b["m"][g] <= b["num_pairs"][g]
+        # at most C(k,3) triangles when m >= C(k-1,2): a loose bound from m
+        assert b["total"][g] <= b["m"][g] ** 1.5
+    for g in list(range(0, num, 97))[:40]:
+        spec = inputs.batch_member(b["seed"], g)
+        src, dst = spec.generate()
+        assert spec.n == b["n"][g] and src.size == b["num_pairs"][g]
+        assert _digest16(src, dst) == b["pairs_sha256_16"][g], g
+    assert math.isclose(sum(b["m"]), 7.236e8, rel_tol=1e-3)
+
+
+def test_stored_top_band_requests_belong_to_the_stream():
+    """tests/golden/serve_top_oracle.json (make_golden.py --serve-top): the
+    first 32 requests of the served stream in the 2^20..2^22-pair band."""
+    with open(os.path.join(os.path.dirname(GOLDEN), "serve_top_oracle.json")) as f:
+        t = json.load(f)
+    lo, hi = t["band"]
+    reqs = t["requests"]
+    assert len(reqs) == 32 and sum(r["num_pairs"] for r in reqs) > (1 << 26)
+    rs = [r["r"] for r in reqs]
+    want = [r for r in range(rs[-1] + 1) if inputs.serve_request(t["seed"], r).num_pairs >= lo]
+    assert rs == want
+    for r in reqs:
+        sp = inputs.serve_request(t["seed"], r["r"])
+        assert (sp.seed, sp.scale, sp.n, sp.num_pairs) == (r["seed"], r["scale"], r["n"],
+                                                           r["num_pairs"])
+        assert lo <= r["num_pairs"] <= hi and r["m"] <= r["num_pairs"]
+    for r in reqs[:3]:
+        src, dst = inputs.serve_request(t["seed"], r["r"]).generate()
+        assert _digest16(src, dst) == r["pairs_sha256_16"]

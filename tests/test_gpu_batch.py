@@ -2,6 +2,9 @@
 oracle and against counting each graph alone.  Counts are integers: exact."""
 from __future__ import annotations
 
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -149,3 +152,42 @@ def test_components_union_on_the_large_input_path(tc):
     with pytest.raises(tc.TCError) as ei:
         tc.preprocess_components(s, d, vpre)
     assert ei.value.status == tc.TC_EINVAL
+
+
+GOLDEN_BATCH = os.path.join(os.path.dirname(__file__), "golden", "batch4096_oracle.json")
+
+
+def test_full_4096_graph_batch_against_stored_oracle(tc):
+    """The batched workload at its stated size: all 4096 graphs (half
+    G(n,p), half RMAT, n up to 2^16, 8.1e8 pairs) in one autotuned persistent
+    launch, every total compared with the oracle's total for that graph,
+    stored by tests/golden/make_golden.py --batch.  Then the same graphs as
+    one disjoint union (the large-input radix path), counted per component."""
+    with open(GOLDEN_BATCH) as f:
+        gold = json.load(f)
+    num = gold["graphs"]
+    graphs, usrc, udst, vpre = [], [], [], [0]
+    for g in range(num):
+        spec = inputs.batch_member(gold["seed"], g)
+        hs, hd = spec.generate()
+        assert spec.n == gold["n"][g] and hs.size == gold["num_pairs"][g]
+        s, d = torch.from_numpy(hs).cuda(), torch.from_numpy(hd).cuda()
+        graphs.append(tc.preprocess(s, d, spec.n, offsets=32))
+        usrc.append(s + vpre[-1])
+        udst.append(d + vpre[-1])
+        vpre.append(vpre[-1] + spec.n)
+    assert [g.stats()["m"] for g in graphs] == gold["m"]
+    b = tc.Batch(graphs)
+    b.autotune(reps=1)
+    got = b.count().cpu().numpy().tolist()
+    assert got == gold["total"]
+    assert b.count_stats()["triangles"] == sum(gold["total"])
+    b.free()
+    for g in graphs:
+        g.free()
+    s, d = torch.cat(usrc), torch.cat(udst)
+    del usrc, udst
+    assert s.shape[0] > (1 << 26)
+    gu = tc.preprocess_components(s, d, vpre)
+    assert tc.count_components(gu).cpu().numpy().tolist() == gold["total"]
+    gu.free()
