@@ -255,7 +255,7 @@ def run_reference(args, wl):
     kind = wl["kind"]
     metric, unit = METRICS[kind]
     if kind == "rmat":
-        scale = min(wl["scale"], args.cpu_sample_scale - 1)
+        scale = min(wl["scale"], args.cpu_sample_scale)   # the sample cpu_baseline times
         specs = [inputs.rmat_graph(args.seed, scale, wl["edge_factor"])]
         sample = (f"RMAT scale {scale}, edge factor {wl['edge_factor']} per step"
                   + (" (the whole workload)" if scale == wl["scale"] else ""))
@@ -314,19 +314,48 @@ def make_inputs(wl, seed, torch, tc, inputs):
             "host-generated seeded Chung-Lu, uploaded before timing")
 
 
-def cpu_baseline(args):
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+def cpu_baseline(args, per_vertex):
+    """The oracle (one thread) and the OpenMP counter (all host cores) on the
+    same bounded sample: RMAT scale cpu_sample_scale of the workload's family
+    (the sample the reference arm times too)."""
+    import cpu_parallel
     import oracle
     from paper_1907_09575_gb300 import inputs
     oracle.build()
+    cpu_parallel.build()
     spec = inputs.rmat_graph(args.seed, args.cpu_sample_scale, 16)
     src, dst = spec.generate()
     t0 = time.perf_counter()
     total, st = oracle.count(src, dst, spec.n, stats=True)
     dt = time.perf_counter() - t0
-    return {"value": st["m"] / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
-            "sample": f"RMAT scale {args.cpu_sample_scale}, edge factor 16 ({spec.num_pairs} pairs, "
-                      f"m={st['m']}, {total} triangles): the oracle's preprocess+count, "
-                      f"single thread, {dt:.1f} s", "seconds": dt}
+    sample = (f"RMAT scale {args.cpu_sample_scale}, edge factor 16 ({spec.num_pairs} pairs, "
+              f"m={st['m']}, {total} triangles)")
+    base = {"value": st["m"] / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sample}: the oracle's preprocess+count, single thread, {dt:.1f} s",
+            "seconds": dt}
+    cpu_parallel.count(src, dst, spec.n, per_vertex=per_vertex)           # warm (threads, pages)
+    t0 = time.perf_counter()
+    ptotal, _, pst = cpu_parallel.count(src, dst, spec.n, per_vertex=per_vertex)
+    pdt = time.perf_counter() - t0
+    assert ptotal == total, (ptotal, total)
+    par = {"value": pst["m"] / pdt, "unit": "edges/s", "cores": pst["threads"],
+           "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+           "kind": "OpenMP shared-memory <j,i,k> map-based counter (cpu_parallel/)",
+           "sample": f"{sample}: preprocess+count" + (" with per-vertex counts" if per_vertex else "")
+                     + f", {pst['threads']} threads, {pdt:.2f} s; total equals the oracle's",
+           "seconds": pdt}
+    return base, par
 
 
 def run_ours(args, wl):
@@ -464,8 +493,8 @@ def run_ours(args, wl):
         (e2e_s,), _ = reduce_over_ranks([e2e_s], [])
         e2e_total = r[0] if isinstance(r, tuple) else r
         assert e2e_total == total, (e2e_total, total)
-        split = {k: (sum(x[k] for x in splits) / len(splits) if k != "input_pinned"
-                     else all(x[k] for x in splits)) for k in splits[0]}
+        split = {k: (sum(x[k] for x in splits) / len(splits) if isinstance(splits[0][k], float)
+                     else splits[-1][k]) for k in splits[0]}
         e2e = {"value": m_all / e2e_s, "unit": "edges/s", "ms_per_step": e2e_s * 1e3,
                "h2d_bytes_per_step": 8 * num_pairs,
                "d2h_bytes_per_step": 8 + (8 * n if wl["per_vertex"] else 0),
@@ -475,9 +504,9 @@ def run_ours(args, wl):
                "torch_pinned_h2d_gbs": torch_h2d_gbs}
         del hs, hd, hpv
 
-    cpu = None
+    cpu = cpu_par = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args)
+        cpu, cpu_par = cpu_baseline(args, wl["per_vertex"])
 
     if ws > 1:
         dist.barrier()
@@ -502,6 +531,7 @@ def run_ours(args, wl):
                        "kernels": {k: [v[0], round(v[1], 3)] for k, v in cprof.items()}},
         "roofline": roof,
         "cpu_baseline": cpu,
+        "cpu_parallel": cpu_par,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,

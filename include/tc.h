@@ -205,13 +205,60 @@ TC_API tc_status tc_triangles(const int32_t* src_host, const int32_t* dst_host, 
  *   h2d_issue_ms     host time spent issuing the upload (as long as the copy
  *                    itself when the pairs are pageable host memory)
  *   input_pinned     1 if both pair arrays are page-locked host memory
+ *   upload_method    1: the copy engine; 2: SM loads over the CPU-GPU link
+ *                    (page-locked input only).  Uploads of 2^27 pairs or more
+ *                    time a 128 MB slice each way and send the rest by the
+ *                    faster; smaller ones use SM loads.
  * TC_EINVAL on NULL out or when this thread made no successful call. */
 typedef struct {
     double wall_ms, h2d_ms, preprocess_ms, count_ms, d2h_ms, h2d_issue_ms;
     int32_t input_pinned;
-    int32_t pad;
+    int32_t upload_method;
 } tc_triangles_timing;
 TC_API tc_status tc_triangles_get_timing(tc_triangles_timing* out);
+
+/*
+ * Graphs larger than the device budget (Section 5.1, Eq. 4 and Eq. 5: the
+ * paper's blocks of U and L with their shifts, as tiles streamed through
+ * device memory on one GPU).
+ *
+ * tc_graph_offload -- moves the graph's count arrays (U in CSR, the <j,i,k>
+ *   tasks, the relabelling) into page-locked host memory and frees its
+ *   device arena.  Afterwards only tc_count_tiled, tc_graph_get_stats and
+ *   tc_graph_free accept the graph (tc_count and the batch calls return
+ *   TC_EINVAL).  A second call does nothing.  Synchronises the stream.
+ *   Errors: TC_EINVAL for NULL g or a graph with components; TC_ENOMEM when
+ *   host memory cannot be page-locked (the graph is then unchanged); TC_ECUDA.
+ *
+ * tc_count_tiled -- Eq. 1 / Eq. 2 on an offloaded graph using at most
+ *   device_budget_bytes of device memory, all of it taken from `alloc`
+ *   (NULL: the library's pool) on `stream` and given back before return.
+ *   Pivots are split into blocks whose rows and tasks fit, rows into blocks
+ *   whose entries fit two buffers; each (row block, pivot block) tile is
+ *   counted by the ordinary count kernel while the next row block uploads
+ *   on a second stream.  The budget must hold 8 B per vertex when per-vertex
+ *   counts are asked for, and the largest row (several times over).
+ *     total_host       receives the total (required).
+ *     per_vertex_host  NULL, or n host uint64 receiving, per ORIGINAL vertex,
+ *                      the triangles through it.
+ *     stats            NULL, or receives the tiling's figures.
+ *   Synchronises the stream.  Errors: TC_EINVAL for NULL g or total_host or
+ *   a graph not offloaded; TC_ENOMEM when the budget is too small (message
+ *   says why) or an allocation fails; TC_ECUDA.
+ */
+typedef struct {
+    int64_t pivot_blocks;   /* blocks of pivots (a pivot with many tasks may span several) */
+    int64_t row_blocks;     /* blocks of rows whose tails the tasks probe */
+    int64_t tiles;          /* (row block, pivot block) pairs counted */
+    int64_t tile_tasks;     /* tasks counted over all tiles (= the graph's tasks) */
+    int64_t h2d_bytes;      /* bytes uploaded */
+    uint64_t probes;        /* tail entries probed (= tc_graph_stats.probes) */
+    int64_t split_pivots;   /* pivots whose tasks were spread over several pivot blocks */
+} tc_tiled_stats;
+TC_API tc_status tc_graph_offload(tc_graph* g, void* stream);
+TC_API tc_status tc_count_tiled(const tc_graph* g, int64_t device_budget_bytes, const tc_allocator* alloc,
+                                const tc_tuning* tune, uint64_t* total_host, uint64_t* per_vertex_host,
+                                tc_tiled_stats* stats, void* stream);
 
 /* Work done by the last tc_count on a graph, read from device counters:
  * index 0 is the warp kernel (pivots with |U_j| <= small_max_outdeg), index 1

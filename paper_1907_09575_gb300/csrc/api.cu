@@ -152,7 +152,12 @@ static void graph_release(tc_graph* g) {
         if (g->arena) g->alloc.put(g->arena, g->arena_bytes);
     } catch (const Error&) {
     }
+    host_copy_free(g->host);
     delete g;
+}
+
+static void need_device_graph(const tc_graph* g, const char* fn) {
+    if (g && g->host) TC_FAIL(TC_EINVAL, "%s: the graph was offloaded to host memory (use tc_count_tiled)", fn);
 }
 
 }  // namespace tc
@@ -266,6 +271,7 @@ tc_status tc_count_components(const tc_graph* g, const tc_tuning* tune, uint64_t
                               void* stream) {
     TC_API_BEGIN
     if (!g || !comp_totals_dev) TC_FAIL(TC_EINVAL, "tc_count_components: NULL argument");
+    need_device_graph(g, "tc_count_components");
     if (g->num_comps <= 0 || !g->comp)
         TC_FAIL(TC_EINVAL, "tc_count_components: graph was not preprocessed with components");
     tc_tuning t;
@@ -282,6 +288,7 @@ tc_status tc_count(const tc_graph* g, const tc_tuning* tune, uint64_t* total_hos
     if (!g) TC_FAIL(TC_EINVAL, "tc_count: graph is NULL");
     if (!total_host && !total_dev && !per_vertex_dev)
         TC_FAIL(TC_EINVAL, "tc_count: no output requested");
+    need_device_graph(g, "tc_count");
     tc_tuning t;
     tuning_resolve(tune, &t);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -346,6 +353,7 @@ tc_status tc_triangles(const int32_t* src_host, const int32_t* dst_host, int64_t
     }
     if (pv) g->alloc.put(pv, sizeof(uint64_t) * n);
     tm.h2d_issue_ms = g->upload_issue_ms;
+    tm.upload_method = g->upload_method;
     g->ev_uploaded = nullptr;
     graph_release(g);
     tm.h2d_ms = ev.ms(0, 1);
@@ -376,9 +384,47 @@ tc_status tc_graph_get_stats(const tc_graph* g, tc_graph_stats* out) {
     TC_API_END
 }
 
+tc_status tc_graph_offload(tc_graph* g, void* stream) {
+    TC_API_BEGIN
+    if (!g) TC_FAIL(TC_EINVAL, "tc_graph_offload: graph is NULL");
+    graph_offload(g, static_cast<cudaStream_t>(stream));
+    TC_API_END
+}
+
+tc_status tc_count_tiled(const tc_graph* g, int64_t device_budget_bytes, const tc_allocator* alloc,
+                         const tc_tuning* tune, uint64_t* total_host, uint64_t* per_vertex_host,
+                         tc_tiled_stats* stats, void* stream) {
+    TC_API_BEGIN
+    if (!g || !total_host) TC_FAIL(TC_EINVAL, "tc_count_tiled: NULL graph or total_host");
+    if (!g->host) TC_FAIL(TC_EINVAL, "tc_count_tiled: the graph is on the device (tc_graph_offload first)");
+    if (alloc && (!alloc->alloc || !alloc->free))
+        TC_FAIL(TC_EINVAL, "tc_count_tiled: allocator without alloc/free");
+    tc_tuning t;
+    tuning_resolve(tune, &t);
+    Alloc al;
+    al.stream = static_cast<cudaStream_t>(stream);
+    if (alloc) {
+        al.user = *alloc;
+        al.has_user = true;
+    }
+    TiledStats ts;
+    count_tiled(g, device_budget_bytes, al, t, total_host, per_vertex_host, &ts, al.stream);
+    if (stats) {
+        stats->pivot_blocks = ts.pivot_blocks;
+        stats->row_blocks = ts.row_blocks;
+        stats->tiles = ts.tiles;
+        stats->tile_tasks = ts.tile_tasks;
+        stats->h2d_bytes = ts.h2d_bytes;
+        stats->probes = ts.probes;
+        stats->split_pivots = ts.split_pivots;
+    }
+    TC_API_END
+}
+
 tc_status tc_count_get_stats(const tc_graph* g, tc_count_stats* out, void* stream) {
     TC_API_BEGIN
     if (!g || !out) TC_FAIL(TC_EINVAL, "tc_count_get_stats: NULL argument");
+    need_device_graph(g, "tc_count_get_stats");
     unsigned long long c[CTR_COUNT];
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     TC_CUDA(cudaMemcpyAsync(c, g->counters, sizeof(c), cudaMemcpyDeviceToHost, st));

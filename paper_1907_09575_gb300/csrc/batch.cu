@@ -163,8 +163,10 @@ tc_status tc_batch_create(const tc_graph* const* graphs, int32_t num, const tc_t
                           void* stream, tc_batch** out) {
     TC_API_BEGIN
     if (!graphs || num <= 0 || !out) TC_FAIL(TC_EINVAL, "tc_batch_create: need graphs, num > 0, out");
-    for (int32_t k = 0; k < num; ++k)
+    for (int32_t k = 0; k < num; ++k) {
         if (!graphs[k]) TC_FAIL(TC_EINVAL, "tc_batch_create: graph %d is NULL", k);
+        if (graphs[k]->host) TC_FAIL(TC_EINVAL, "tc_batch_create: graph %d was offloaded to host memory", k);
+    }
     tc_batch* b = new tc_batch();
     try {
         b->num = num;

@@ -175,12 +175,26 @@ struct tc_graph {
     // host time spent issuing the upload (long when the source is pageable)
     cudaEvent_t ev_uploaded = nullptr;
     double upload_issue_ms = 0.0;
+    int upload_method = 0;      // 1 copy engine, 2 SM loads of page-locked memory
+
+    // after tc_graph_offload: the count's arrays in page-locked host memory
+    // (and no device arena)
+    struct HostCopy* host = nullptr;
 
     int64_t n_tasks = 0, n_small = 0, n_large = 0;
     void* units_mem = nullptr;      // small units, then large units
     size_t units_bytes = 0;
     tc_tuning units_tuning{};       // tuning the unit lists were built for
     tc_graph_stats stats{};
+};
+
+// Page-locked host copies of a graph's count arrays (tc_graph_offload).
+struct HostCopy {
+    void* off = nullptr;        // n+1, int32 or int64 as tc_graph::off64
+    int32_t* adj = nullptr;     // m
+    int64_t* loff = nullptr;    // n+1
+    struct Task* tasks = nullptr;   // n_tasks
+    int32_t* perm = nullptr;    // n
 };
 
 // A <j,i,k> task: edge (i,j) of U with the part of U_i after j nonempty.
@@ -213,7 +227,8 @@ struct GraphView {
     unsigned long long* comp_totals;   // per-component totals (with comp)
     int64_t n;
     int32_t off64;
-    int32_t pad;
+    int32_t jbase;                // label of local pivot 0 (tiles of a host-resident
+                                  // graph index pivots from their block's start)
 };
 
 // Device counters of one count: queue heads, the total, and work done by the

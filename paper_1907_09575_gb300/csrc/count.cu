@@ -44,6 +44,12 @@ constexpr int kEmpty = -1;
 #define TC_UNROLL 4
 #endif
 constexpr int kUnroll = TC_UNROLL;   // independent loads in flight per lane
+#ifndef TC_PV_WALK
+#define TC_PV_WALK 0           // per-vertex long walk: 0 checked rounds, 1 unchecked full rounds
+#endif
+#ifndef TC_PV_BRANCHLESS
+#define TC_PV_BRANCHLESS 1     // per-vertex bitmap probe: 1 computes the rank on every lane
+#endif
 // warp unit table region: 128 hash slots, or a 128-word bitmap (4095 labels
 // and the guard bit)
 // plus its 128 16-bit rank prefixes
@@ -119,6 +125,18 @@ struct BitTab {
         const unsigned d = offset(k);
         return (bm[d >> 5] >> (d & 31)) & 1u;
     }
+    // membership and rank without a branch on the membership: the rank is
+    // read for every probe (the guard bit's word has a prefix too), and only
+    // the credit is predicated on the hit
+    __device__ __forceinline__ void probe_credit(int k, unsigned* cnt, unsigned& mine) const {
+        const unsigned d = offset(k);
+        const unsigned w = bm[d >> 5];
+        const unsigned b = d & 31;
+        const unsigned h = (w >> b) & 1u;
+        const int r = (int)pre[d >> 5] + __popc(w & ((1u << b) - 1u));
+        mine += h;
+        if (h) atomicAdd(&cnt[r], 1u);
+    }
     // hit counters by rank (rank < slice <= 4096): one word each, so hits on
     // neighbouring entries never share an atomic's word
     __device__ __forceinline__ void credit(unsigned* cnt, int r) const { atomicAdd(&cnt[r], 1u); }
@@ -172,10 +190,21 @@ __device__ __forceinline__ unsigned hash_buckets(int dp) {
 }
 
 
+template <class Tab>
+struct has_probe_credit {
+    template <class U>
+    static constexpr bool check(decltype(&U::probe_credit)) { return true; }
+    template <class U>
+    static constexpr bool check(...) { return false; }
+    static constexpr bool value = check<Tab>(nullptr);
+};
+
 template <bool PV, class Tab>
 __device__ __forceinline__ void probe_one(const Tab& T, int k, unsigned* cnt, unsigned& mine) {
     if constexpr (!PV) {
         mine += T.bit(k);
+    } else if constexpr (TC_PV_BRANCHLESS && has_probe_credit<Tab>::value) {
+        T.probe_credit(k, cnt, mine);
     } else {
         const int r = T.template find<PV>(k);
         if (r >= 0) {
@@ -201,7 +230,40 @@ __device__ __forceinline__ unsigned warp_walk_tail(int64_t st, int L, const int3
     const int lane = threadIdx.x & 31;
     const int32_t* __restrict__ p = adj + st + lane;
     unsigned mine = 0;
-    if constexpr (PV) {
+    if constexpr (PV && TC_PV_WALK == 1) {
+        // full rounds unchecked, each loading the next full round before it
+        // probes; then one checked round for the rest
+        constexpr int R = 32 * kUnroll;
+        const int full = L - L % R;
+        int q0 = 0;
+        if (full > 0) {
+            int k[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) k[u] = __ldg(p + 32 * u);
+            for (; q0 + R < full; q0 += R) {
+                int kn[kUnroll];
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) kn[u] = __ldg(p + q0 + R + 32 * u);
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) probe_one<PV>(T, k[u], cnt, mine);
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) k[u] = kn[u];
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) probe_one<PV>(T, k[u], cnt, mine);
+            q0 = full;
+        }
+        if (q0 < L) {
+            int k[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) k[u] = (q0 + 32 * u + lane < L) ? __ldg(p + q0 + 32 * u) : -1;
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                if (k[u] >= 0) probe_one<PV>(T, k[u], cnt, mine);
+        }
+        hits += mine;
+        return __reduce_add_sync(0xffffffffu, mine);
+    } else if constexpr (PV) {
         int k[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) k[u] = (32 * u + lane < L) ? __ldg(p + 32 * u) : -1;
@@ -473,7 +535,7 @@ __device__ __forceinline__ void warp_unit(const GraphView& G, const Unit& U, uns
     hits += uh;
     if (PV) {
         uh = warp_sum_u64(uh);
-        if (lane == 0 && uh) atomicAdd(&G.tnew[U.j], (unsigned long long)uh);
+        if (lane == 0 && uh) atomicAdd(&G.tnew[G.jbase + U.j], (unsigned long long)uh);
     }
     __syncwarp();
 }
@@ -639,7 +701,7 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
         if (threadIdx.x == 0) {
             unsigned long long tot = 0;
             for (int q = 0; q < nw; ++q) tot += s_red[q];
-            if (tot) atomicAdd(&G.tnew[U.j], tot);
+            if (tot) atomicAdd(&G.tnew[G.jbase + U.j], tot);
         }
     }
 }

@@ -91,4 +91,16 @@ void count_components(const tc_graph* g, const tc_tuning& t, uint64_t* comp_tota
 void attach_components(tc_graph* g, const int32_t* src_dev, const int32_t* dst_dev, int64_t P,
                        const int64_t* vpre_host, int32_t num_comps, cudaStream_t st);
 
+// Out-of-core count (tiled.cu).  graph_offload moves the count's arrays to
+// page-locked host memory and frees the device arena; count_tiled counts
+// such a graph within `budget` bytes of device memory taken from `al`.
+struct TiledStats {
+    int64_t pivot_blocks = 0, row_blocks = 0, tiles = 0, tile_tasks = 0, h2d_bytes = 0, split_pivots = 0;
+    uint64_t probes = 0;
+};
+void graph_offload(tc_graph* g, cudaStream_t st);
+void host_copy_free(HostCopy* h);
+void count_tiled(const tc_graph* g, int64_t budget, Alloc& al, const tc_tuning& t, uint64_t* total_host,
+                 uint64_t* per_vertex_host, TiledStats* ts, cudaStream_t st);
+
 }  // namespace tc

@@ -70,7 +70,7 @@ EXPORTS = ("tc_preprocess", "tc_count", "tc_triangles", "tc_graph_get_stats", "t
            "tc_server_create", "tc_server_now", "tc_server_submit_rmat", "tc_server_poll",
            "tc_server_drain", "tc_server_get_stats", "tc_server_free", "tc_release_memory",
            "tc_selftest_wait_timeout", "tc_server_submit_rmat_many", "tc_memory_get_stats",
-           "tc_triangles_get_timing")
+           "tc_triangles_get_timing", "tc_graph_offload", "tc_count_tiled")
 
 TC_STATIC_MAX_PAIRS = 262144
 TC_STATIC_MAX_VERTICES = 65536
@@ -116,7 +116,13 @@ class MemoryStats(ctypes.Structure):
 class TrianglesTiming(ctypes.Structure):
     _fields_ = [(f, ctypes.c_double) for f in ("wall_ms", "h2d_ms", "preprocess_ms", "count_ms",
                                                 "d2h_ms", "h2d_issue_ms")] + \
-               [("input_pinned", ctypes.c_int32), ("pad", ctypes.c_int32)]
+               [("input_pinned", ctypes.c_int32), ("upload_method", ctypes.c_int32)]
+
+
+class TiledStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("pivot_blocks", "row_blocks", "tiles", "tile_tasks",
+                                               "h2d_bytes")] + [("probes", ctypes.c_uint64),
+                                                                ("split_pivots", ctypes.c_int64)]
 
 
 class KernelTime(ctypes.Structure):
@@ -171,6 +177,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tc_memory_get_stats.restype = st
     lib.tc_triangles_get_timing.argtypes = [ctypes.POINTER(TrianglesTiming)]
     lib.tc_triangles_get_timing.restype = st
+    lib.tc_graph_offload.argtypes = [vp, vp]
+    lib.tc_graph_offload.restype = st
+    lib.tc_count_tiled.argtypes = [vp, i64, vp, vp, vp, vp, ctypes.POINTER(TiledStats), vp]
+    lib.tc_count_tiled.restype = st
     lib.tc_server_poll.argtypes = [vp, ctypes.POINTER(ServerResult), i32, ctypes.POINTER(i32), i32]
     lib.tc_server_poll.restype = st
     lib.tc_server_drain.argtypes = [vp, i32]
@@ -334,6 +344,29 @@ class Graph:
         if per_vertex is True:
             return t, pv[: self.n]
         return t
+
+
+    def offload(self, stream=None) -> None:
+        """tc_graph_offload: move the count's arrays to page-locked host
+        memory and free the device arena (then only count_tiled counts it)."""
+        _check(load().tc_graph_offload(self._h, _stream_ptr(stream)))
+
+    def count_tiled(self, budget_bytes: int, per_vertex: bool = False,
+                    allocator: Optional[Allocator] = None, tuning: Optional[Tuning] = None,
+                    stream=None):
+        """tc_count_tiled: count an offloaded graph within budget_bytes of
+        device memory.  Returns (total, per-vertex uint64 numpy or None,
+        tiling stats)."""
+        total = ctypes.c_uint64(0)
+        pv = np.zeros(max(self.n, 1), dtype=np.uint64) if per_vertex else None
+        ts = TiledStats()
+        _check(load().tc_count_tiled(self._h, int(budget_bytes),
+                                     ctypes.byref(allocator) if allocator is not None else None,
+                                     ctypes.byref(tuning) if tuning is not None else None,
+                                     ctypes.addressof(total), pv.ctypes.data if pv is not None else None,
+                                     ctypes.byref(ts), _stream_ptr(stream)))
+        return (int(total.value), pv[: self.n] if pv is not None else None,
+                {f: int(getattr(ts, f)) for f, _ in TiledStats._fields_})
 
 
 class Batch:
@@ -552,8 +585,10 @@ def triangles_timing() -> dict:
     tc_triangles call (device phases from CUDA events, wall time on the host)."""
     t = TrianglesTiming()
     _check(load().tc_triangles_get_timing(ctypes.byref(t)))
-    return {f: (bool(t.input_pinned) if f == "input_pinned" else float(getattr(t, f)))
-            for f, _ in TrianglesTiming._fields_ if f != "pad"}
+    out = {f: float(getattr(t, f)) for f, _ in TrianglesTiming._fields_[:6]}
+    out["input_pinned"] = bool(t.input_pinned)
+    out["upload_method"] = {1: "copy engine", 2: "SM loads"}.get(int(t.upload_method), "none")
+    return out
 
 
 def triangles_static(src, dst, n: int, per_vertex=None, stream=None) -> int:

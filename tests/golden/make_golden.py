@@ -11,6 +11,9 @@
   workloads, RMAT scale 26 (edge factor 16, seed 1) and the Chung-Lu graph
   (5e7 vertices, seed 1): total, a digest of the per-vertex counts, the
   graph statistics.
+* ``fullsize_parallel.json`` (``--fullsize-parallel``): the same two graphs
+  counted by the OpenMP shared-memory counter in ``cpu_parallel/``, which
+  shares no code with the oracle -- a second, independent count at full size.
 * ``batch4096_oracle.json`` (``--batch``, a few minutes on all host cores):
   the oracle's total for every one of the 4096 graphs of the batched
   workload (seed 1), with each graph's size and a digest of its pairs.
@@ -18,10 +21,11 @@
   first 32 requests of the served stream (seed 1) whose pair count lies in
   the top band, 2^20..2^22 pairs; together they hold more than 2^26 pairs,
   so a tick carrying all of them takes the large-input deduplication path.
-Only ``oracle/`` and the seeded input generators are called.
+Only ``oracle/`` (``cpu_parallel/`` for ``--fullsize-parallel``) and the
+seeded input generators are called.
 
 Run from the repository root:
-  python tests/golden/make_golden.py [--fullsize | --batch | --serve-top]
+  python tests/golden/make_golden.py [--fullsize | --fullsize-parallel | --batch | --serve-top]
 """
 from __future__ import annotations
 
@@ -154,6 +158,24 @@ def fullsize():
     return res
 
 
+def fullsize_parallel():
+    import time
+    import cpu_parallel
+    from paper_1907_09575_gb300 import inputs
+    res = {}
+    for name, spec in (("rmat-s26", inputs.rmat_graph(1, 26, 16)), ("chunglu", inputs.chung_lu_graph(1))):
+        src, dst = spec.generate()
+        t0 = time.perf_counter()
+        total, t, st = cpu_parallel.count(src, dst, spec.n, per_vertex=True)
+        dt = time.perf_counter() - t0
+        res[name] = dict(n=spec.n, num_pairs=int(src.shape[0]), total=total,
+                         per_vertex_sha256=hashlib.sha256(t.astype("<u8").tobytes()).hexdigest(),
+                         m=st["m"], max_outdeg=st["max_outdeg"], max_deg=st["max_deg"],
+                         threads=st["threads"], seconds=round(dt, 1))
+        del src, dst, t
+    return res
+
+
 def _pairs_digest(src, dst) -> str:
     return hashlib.sha256(src.astype("<i4").tobytes() + dst.astype("<i4").tobytes()).hexdigest()
 
@@ -212,7 +234,8 @@ def serve_top(seed=1, count=32, lo=1 << 20):
 
 
 if __name__ == "__main__":
-    for flag, fn, name in (("--batch", batch4096, "batch4096_oracle.json"),
+    for flag, fn, name in (("--fullsize-parallel", fullsize_parallel, "fullsize_parallel.json"),
+                           ("--batch", batch4096, "batch4096_oracle.json"),
                            ("--serve-top", serve_top, "serve_top_oracle.json")):
         if flag in sys.argv:
             out = fn()

@@ -74,8 +74,8 @@ int main(void) {
          offsetof(tc_tuning, slice_max));
   printf("%zu %zu %zu %zu\n", sizeof(tc_server_result), offsetof(tc_server_result, tick_pairs),
          sizeof(tc_server_stats), offsetof(tc_server_stats, device_overlap_s));
-  printf("%zu %zu %zu %zu\n", sizeof(tc_memory_stats), sizeof(tc_rmat_spec), sizeof(tc_server_config),
-         sizeof(tc_triangles_timing));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(tc_memory_stats), sizeof(tc_rmat_spec), sizeof(tc_server_config),
+         sizeof(tc_triangles_timing), sizeof(tc_tiled_stats));
   return 0;
 }
 '''
@@ -96,7 +96,8 @@ int main(void) {
                                           tc.ServerStats.device_overlap_s.offset]
     assert [int(x) for x in e.split()] == [ctypes.sizeof(tc.MemoryStats), ctypes.sizeof(tc.RmatSpec),
                                           ctypes.sizeof(tc.ServerConfig),
-                                          ctypes.sizeof(tc.TrianglesTiming)]
+                                          ctypes.sizeof(tc.TrianglesTiming),
+                                          ctypes.sizeof(tc.TiledStats)]
 
 
 def test_missing_library_fails_loudly(tmp_path):

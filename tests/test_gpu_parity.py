@@ -312,3 +312,30 @@ def test_invalid_id_on_the_sort_path(tc):
     g = tc.preprocess(s, d, n)
     assert g.stats()["m"] > 0 and g.count() > 0
     g.free()
+
+
+def test_pinned_host_input_paths(tc):
+    """Host pairs in page-locked memory are uploaded by SM loads (vector or,
+    for a buffer not 16-byte aligned, scalar); pageable ones by the copy
+    engine.  All give the oracle's counts, through tc_preprocess and
+    tc_triangles."""
+    spec = inputs.rmat_graph(4, 15, 16)
+    hs, hd = spec.generate()
+    want, want_t = oracle.count(hs, hd, spec.n, per_vertex=True)
+    ps = torch.empty(hs.size + 1, dtype=torch.int32, pin_memory=True)
+    pd = torch.empty(hd.size + 1, dtype=torch.int32, pin_memory=True)
+    for off in (0, 1):                     # aligned, then one element in
+        ps[off:off + hs.size] = torch.from_numpy(hs)
+        pd[off:off + hd.size] = torch.from_numpy(hd)
+        a = ps[off:off + hs.size].numpy()
+        b = pd[off:off + hd.size].numpy()
+        g = tc.preprocess(a, b, spec.n)
+        total, t = g.count(per_vertex=True)
+        g.free()
+        assert total == want and np.array_equal(t.cpu().numpy().astype(np.uint64), want_t)
+        total2, t2 = tc.triangles(a, b, spec.n, per_vertex=True)
+        assert total2 == want and np.array_equal(t2.astype(np.uint64), want_t)
+        tm = tc.triangles_timing()
+        assert tm["input_pinned"] and tm["h2d_ms"] >= 0 and tm["count_ms"] > 0
+    total3 = tc.triangles(hs, hd, spec.n)   # pageable
+    assert total3 == want and not tc.triangles_timing()["input_pinned"]
