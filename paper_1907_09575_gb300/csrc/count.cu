@@ -50,6 +50,9 @@ constexpr int kUnroll = TC_UNROLL;   // independent loads in flight per lane
 #ifndef TC_PV_BRANCHLESS
 #define TC_PV_BRANCHLESS 1     // per-vertex bitmap probe: 1 computes the rank on every lane
 #endif
+#ifndef TC_PV_PRED_RED
+#define TC_PV_PRED_RED 0       // per-hit shared counter add: 1 as one predicated red (no branch)
+#endif
 // warp unit table region: 128 hash slots, or a 128-word bitmap (4095 labels
 // and the guard bit)
 // plus its 128 16-bit rank prefixes
@@ -135,7 +138,13 @@ struct BitTab {
         const unsigned h = (w >> b) & 1u;
         const int r = (int)pre[d >> 5] + __popc(w & ((1u << b) - 1u));
         mine += h;
+#if TC_PV_PRED_RED
+        const unsigned a = (unsigned)__cvta_generic_to_shared(&cnt[r]);
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\t@p red.shared.add.u32 [%0], 1;\n\t}"
+                     ::"r"(a), "r"(h) : "memory");
+#else
         if (h) atomicAdd(&cnt[r], 1u);
+#endif
     }
     // hit counters by rank (rank < slice <= 4096): one word each, so hits on
     // neighbouring entries never share an atomic's word

@@ -86,3 +86,15 @@ def test_stored_top_band_requests_belong_to_the_stream():
     for r in reqs[:3]:
         src, dst = inputs.serve_request(t["seed"], r["r"]).generate()
         assert _digest16(src, dst) == r["pairs_sha256_16"]
+
+
+def test_parallel_counter_agrees_with_the_oracle_at_full_size(gold):
+    """tests/golden/fullsize_parallel.json (make_golden.py --fullsize-parallel):
+    the OpenMP counter in cpu_parallel/, which shares no code with the oracle,
+    counted both full-size graphs; every stored figure equals the oracle's."""
+    with open(os.path.join(os.path.dirname(GOLDEN), "fullsize_parallel.json")) as f:
+        par = json.load(f)
+    assert set(par) == set(gold)
+    for name, p in par.items():
+        for key in ("n", "num_pairs", "total", "per_vertex_sha256", "m", "max_outdeg", "max_deg"):
+            assert p[key] == gold[name][key], (name, key)
