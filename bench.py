@@ -189,6 +189,35 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def _cpulist(text: str) -> set:
+    cpus = set()
+    for part in text.strip().split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            cpus.update(range(int(a), int(b) + 1))
+        elif part:
+            cpus.add(int(part))
+    return cpus
+
+
+def bind_near_gpu(dev: int) -> str:
+    """Restrict this thread to the CPUs the system lists as local to the GPU
+    (sysfs local_cpulist of its PCI function), so that page-locked buffers it
+    allocates land in the memory next to the GPU.  Returns what was done."""
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        bdf = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        text = open(f"/sys/bus/pci/devices/{bdf}/local_cpulist").read()
+        cpus = _cpulist(text) & os.sched_getaffinity(0)
+        if not cpus:
+            return f"not bound: no allowed CPU in {bdf} local_cpulist {text.strip()}"
+        os.sched_setaffinity(0, cpus)
+        return f"bound to {bdf} local_cpulist {text.strip()} ({len(cpus)} CPUs)"
+    except (OSError, AttributeError, ValueError) as e:
+        return f"not bound: {e}"
+
+
 def peaks() -> tuple[float, str]:
     try:
         with open(PEAKS_FILE) as f:
@@ -462,6 +491,8 @@ def run_ours(args, wl):
     # --- end to end through the one-shot C ABI call, host buffers ------------
     e2e = None
     if not args.no_e2e:
+        affinity = os.sched_getaffinity(0)
+        numa_note = bind_near_gpu(local)
         hs = torch.empty(num_pairs, dtype=torch.int32, pin_memory=True)
         hd = torch.empty(num_pairs, dtype=torch.int32, pin_memory=True)
         hs.copy_(src)
@@ -501,8 +532,9 @@ def run_ours(args, wl):
                "call": "tc_triangles (host pairs in pinned memory -> host total"
                        + (" + per-vertex)" if wl["per_vertex"] else ")"),
                "split_ms": {k: (round(v, 3) if isinstance(v, float) else v) for k, v in split.items()},
-               "torch_pinned_h2d_gbs": torch_h2d_gbs}
+               "torch_pinned_h2d_gbs": torch_h2d_gbs, "host_buffers": numa_note}
         del hs, hd, hpv
+        os.sched_setaffinity(0, affinity)
 
     cpu = cpu_par = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -708,7 +740,8 @@ def run_batch(args, wl):
                            "tuning": "library default"},
         "batch_speedup": ms_one / ms,
         "tuning": {f: getattr(tuning, f) for f in ("small_max_outdeg", "warp_unit_tasks",
-                                                   "cta_unit_tasks", "cta_threads", "slice_max")},
+                                                   "cta_unit_tasks", "cta_threads", "slice_max",
+                                                   "merge_max_outdeg")},
         "autotune_s": tune_s, "setup_s": setup_s,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks, "count_work": kst,

@@ -84,7 +84,10 @@ typedef struct {
     int32_t table_mode;        /* 0: a bitmap when the pivot's label span fits (the
                                   direct-index case of Section 5.2), else a hash;
                                   1: hash tables only (the hashed-pivot ablation) */
-    int32_t reserved[2];
+    int32_t merge_max_outdeg;  /* warp-unit pivots with |U_j| <= this build no table:
+                                  each lane searches the sorted row (the list-based
+                                  traversal of Section 3.1); 0 = never (<= 64) */
+    int32_t reserved;
 } tc_tuning;
 
 /* Graph facts, computed during preprocessing. */
@@ -209,11 +212,14 @@ TC_API tc_status tc_triangles(const int32_t* src_host, const int32_t* dst_host, 
  *                    (page-locked input only).  Uploads of 2^27 pairs or more
  *                    time a 128 MB slice each way and send the rest by the
  *                    faster; smaller ones use SM loads.
+ *   ce_slice_gbs, sm_slice_gbs  the rates of those two timed slices (0 when
+ *                    no slice was timed)
  * TC_EINVAL on NULL out or when this thread made no successful call. */
 typedef struct {
     double wall_ms, h2d_ms, preprocess_ms, count_ms, d2h_ms, h2d_issue_ms;
     int32_t input_pinned;
     int32_t upload_method;
+    double ce_slice_gbs, sm_slice_gbs;
 } tc_triangles_timing;
 TC_API tc_status tc_triangles_get_timing(tc_triangles_timing* out);
 
@@ -348,8 +354,10 @@ TC_API tc_status tc_generate_rmat(uint64_t seed, int32_t scale, int64_t n, int64
  * tc_batch_count: one graph launch on `stream`; if totals_dev is non-NULL it
  *   receives num device uint64 totals, in the order the graphs were given.
  *   Stream ordered; one count at a time per batch.
- * tc_batch_autotune: times candidate tunings (reps replays each) and keeps
- *   the fastest; the choice is cached per degree profile (graph count, mean
+ * tc_batch_autotune: times candidate tunings (reps replays each: warp/CTA
+ *   bin boundary, tasks per warp and per CTA unit, CTA threads, and the
+ *   merge threshold below which short pivot rows are searched rather than
+ *   tabled) and keeps the fastest; the choice is cached per degree profile (graph count, mean
  *   edges, largest pivot row, mean tail length) for later batches in the
  *   process.  *chosen (may be NULL) receives it.  Synchronises `stream`.
  * tc_batch_get_count_stats: work counters of the last tc_batch_count;

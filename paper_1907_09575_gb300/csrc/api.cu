@@ -110,6 +110,7 @@ void tuning_resolve(const tc_tuning* in, tc_tuning* out) {
     }
     if (in->slice_max > 0) out->slice_max = std::max(64, std::min(in->slice_max, kMaxSlice));
     out->table_mode = in->table_mode == 1 ? 1 : 0;
+    out->merge_max_outdeg = std::max(0, std::min(in->merge_max_outdeg, out->small_max_outdeg));
 }
 
 bool tuning_equal(const tc_tuning& a, const tc_tuning& b) {
@@ -354,6 +355,8 @@ tc_status tc_triangles(const int32_t* src_host, const int32_t* dst_host, int64_t
     if (pv) g->alloc.put(pv, sizeof(uint64_t) * n);
     tm.h2d_issue_ms = g->upload_issue_ms;
     tm.upload_method = g->upload_method;
+    tm.ce_slice_gbs = g->upload_probe_gbs[0];
+    tm.sm_slice_gbs = g->upload_probe_gbs[1];
     g->ev_uploaded = nullptr;
     graph_release(g);
     tm.h2d_ms = ev.ms(0, 1);

@@ -258,25 +258,28 @@ tc_status tc_batch_autotune(tc_batch* b, int32_t reps, tc_tuning* chosen, void* 
         const int warp_tasks[] = {64, 512};
         const int cta_tasks[] = {512, 4096};
         const int threads[] = {128, 256};
+        const int merge_max[] = {0, 16};   // short pivot rows searched instead of tabled
         for (int a : small_max)
             for (int w : warp_tasks)
                 for (int c : cta_tasks)
-                    for (int th : threads) {
-                        tc_tuning cand;
-                        tuning_defaults(&cand);
-                        cand.small_max_outdeg = a;
-                        cand.warp_unit_tasks = w;
-                        cand.cta_unit_tasks = c;
-                        cand.cta_threads = th;
-                        tc_tuning res;
-                        tuning_resolve(&cand, &res);
-                        set_tuning(b, res);
-                        const float ms = time_batch(b, std::max(reps, 1), st);
-                        if (ms < best_ms) {
-                            best_ms = ms;
-                            best = b->tuning;
+                    for (int th : threads)
+                        for (int mm : merge_max) {
+                            tc_tuning cand;
+                            tuning_defaults(&cand);
+                            cand.small_max_outdeg = a;
+                            cand.warp_unit_tasks = w;
+                            cand.cta_unit_tasks = c;
+                            cand.cta_threads = th;
+                            cand.merge_max_outdeg = mm;
+                            tc_tuning res;
+                            tuning_resolve(&cand, &res);
+                            set_tuning(b, res);
+                            const float ms = time_batch(b, std::max(reps, 1), st);
+                            if (ms < best_ms) {
+                                best_ms = ms;
+                                best = b->tuning;
+                            }
                         }
-                    }
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[sig] = best;
     }

@@ -176,6 +176,7 @@ struct tc_graph {
     cudaEvent_t ev_uploaded = nullptr;
     double upload_issue_ms = 0.0;
     int upload_method = 0;      // 1 copy engine, 2 SM loads of page-locked memory
+    double upload_probe_gbs[2] = {0.0, 0.0};   // the timed slices: copy engine, SM loads
 
     // after tc_graph_offload: the count's arrays in page-locked host memory
     // (and no device arena)

@@ -50,6 +50,9 @@ constexpr int kUnroll = TC_UNROLL;   // independent loads in flight per lane
 #ifndef TC_PV_BRANCHLESS
 #define TC_PV_BRANCHLESS 1     // per-vertex bitmap probe: 1 computes the rank on every lane
 #endif
+#ifndef TC_PV_ATOM_LOOP
+#define TC_PV_ATOM_LOOP 0      // per-vertex long walk: 1 gathers a round's hits per lane, then loops
+#endif
 #ifndef TC_PV_PRED_RED
 #define TC_PV_PRED_RED 0       // per-hit shared counter add: 1 as one predicated red (no branch)
 #endif
@@ -128,6 +131,14 @@ struct BitTab {
         const unsigned d = offset(k);
         return (bm[d >> 5] >> (d & 31)) & 1u;
     }
+    // the rank and the hit bit of a probe (rank meaningful only on a hit)
+    __device__ __forceinline__ int rank_hit(int k, unsigned& h) const {
+        const unsigned d = offset(k);
+        const unsigned w = bm[d >> 5];
+        const unsigned b = d & 31;
+        h = (w >> b) & 1u;
+        return (int)pre[d >> 5] + __popc(w & ((1u << b) - 1u));
+    }
     // membership and rank without a branch on the membership: the rank is
     // read for every probe (the guard bit's word has a prefix too), and only
     // the credit is predicated on the hit
@@ -182,6 +193,28 @@ struct HashTab {
     }
 };
 
+// Search (the list-based joint traversal of Section 3.1, lane-parallel): the
+// sorted pivot row U_j (at most 64 entries) sits in shared memory and each
+// lane places its probe in it by a branchless binary search.  No table is
+// built; the position found is the entry's index, so per-vertex credit
+// needs no rank.
+struct SearchTab {
+    const int* piv;
+    int dp, lo, hi;
+    template <bool PV>
+    __device__ __forceinline__ int find(int k) const {
+        if ((unsigned)(k - lo) > (unsigned)(hi - lo)) return -1;
+        int pos = 0;
+#pragma unroll
+        for (int step = 32; step > 0; step >>= 1)
+            if (pos + step < dp && piv[pos + step] <= k) pos += step;
+        return piv[pos] == k ? pos : -1;
+    }
+    __device__ __forceinline__ unsigned bit(int k) const { return find<false>(k) >= 0; }
+    __device__ __forceinline__ void credit(unsigned* cnt, int r) const { atomicAdd(&cnt[r], 1u); }
+    __device__ __forceinline__ unsigned credited(const unsigned* cnt, int r) const { return cnt[r]; }
+};
+
 __device__ __forceinline__ void hash_insert(int* tab, unsigned bmask, int k) {
     unsigned b = (unsigned)k & bmask;
     while (true) {
@@ -198,6 +231,32 @@ __device__ __forceinline__ unsigned hash_buckets(int dp) {
     return b;
 }
 
+
+// A round's probes, then each lane's hits credited in a loop: a warp issues
+// as many counter adds as its busiest lane has hits (about 2.6 for 4 probes
+// a lane at a 1-in-5 hit rate) instead of one per probe step.
+template <class Tab>
+__device__ __forceinline__ void probe_round_credit(const Tab& T, const int (&k)[kUnroll], unsigned* cnt,
+                                                   unsigned& mine) {
+    int r[kUnroll];
+    unsigned hm = 0;
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+        unsigned h;
+        r[u] = T.rank_hit(k[u], h);
+        hm |= h << u;
+    }
+    mine += __popc(hm);
+    while (hm) {
+        const int u = __ffs(hm) - 1;
+        hm &= hm - 1u;
+        int rr = r[0];
+#pragma unroll
+        for (int q = 1; q < kUnroll; ++q)
+            if (u == q) rr = r[q];
+        atomicAdd(&cnt[rr], 1u);
+    }
+}
 
 template <class Tab>
 struct has_probe_credit {
@@ -281,9 +340,13 @@ __device__ __forceinline__ unsigned warp_walk_tail(int64_t st, int L, const int3
             int kn[kUnroll];
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) kn[u] = (q1 + 32 * u + lane < L) ? __ldg(p + q1 + 32 * u) : -1;
+            if constexpr (TC_PV_ATOM_LOOP && has_probe_credit<Tab>::value) {
+                probe_round_credit(T, k, cnt, mine);   // k < 0 lands on the clear guard bit
+            } else {
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u)
-                if (k[u] >= 0) probe_one<PV>(T, k[u], cnt, mine);
+                for (int u = 0; u < kUnroll; ++u)
+                    if (k[u] >= 0) probe_one<PV>(T, k[u], cnt, mine);
+            }
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) k[u] = kn[u];
         }
@@ -466,10 +529,10 @@ struct GraphAcc {
 // Warp unit: a pivot with |U_j| <= 64 processed by one warp with a private
 // table (a bitmap of <= 4095 labels, or 128 hash slots).
 // ---------------------------------------------------------------------------
-template <bool PV>
+template <bool PV, bool MERGE>
 __device__ __forceinline__ void warp_unit(const GraphView& G, const Unit& U, unsigned* region,
-                                          unsigned* cnt, int64_t* s_base, bool hash_only, unsigned* tlow,
-                                          uint64_t& hits, uint64_t& probes, uint64_t& staged) {
+                                          unsigned* cnt, int64_t* s_base, bool hash_only, int merge_max,
+                                          unsigned* tlow, uint64_t& hits, uint64_t& probes, uint64_t& staged) {
     const int lane = threadIdx.x & 31;
     const int64_t rb = off_at(G, U.j), re = off_at(G, U.j + 1);
     const int dp = (int)(re - rb);
@@ -480,7 +543,27 @@ __device__ __forceinline__ void warp_unit(const GraphView& G, const Unit& U, uns
     uint64_t uh = 0;
     if (PV)
         for (int s = lane; s < kSmallTable / 2; s += 32) cnt[s] = 0;
-    if (bitmap) {
+    if (MERGE && dp <= merge_max) {
+        int* piv = reinterpret_cast<int*>(region);
+        if (lane < dp) piv[lane] = mine;
+        if (lane + 32 < dp) piv[lane + 32] = mine2;
+        __syncwarp();
+        const SearchTab T{piv, dp, lo, hi};
+        for (int64_t tb = U.t0; tb < U.t1; tb += 32)
+            warp_probe_group<PV>(G.tasks, tb, U.t1, G.adj, T, cnt, G.tnew, tlow, s_base, U.t0, nullptr,
+                                 nullptr, uh, probes);
+        __syncwarp();
+        if (PV) {
+            if (lane < dp) {
+                const unsigned h = T.credited(cnt, lane);
+                if (h) atomicAdd(&G.tnew[mine], (unsigned long long)h);
+            }
+            if (lane + 32 < dp) {
+                const unsigned h = T.credited(cnt, lane + 32);
+                if (h) atomicAdd(&G.tnew[mine2], (unsigned long long)h);
+            }
+        }
+    } else if (bitmap) {
         const int words = ((hi - lo + 1) >> 5) + 1;
         for (int s = lane; s < words; s += 32) region[s] = 0;
         __syncwarp();
@@ -725,11 +808,11 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
 // (kRegionWords words; warp units use 192-word slices of it) | hit counters
 // (PV: kRegionWords/2 words) | long-task queue (unit_tasks x 16 bit).
 // ---------------------------------------------------------------------------
-template <bool PV>
+template <bool PV, bool MERGE>
 __global__ void __launch_bounds__(256, TC_LARGE_MINB)
     k_count(const GraphView* __restrict__ views, const Unit* __restrict__ large, int64_t nlarge,
             const Unit* __restrict__ small, int64_t nsmall, int slice_max, int table_mode,
-            unsigned* tlow, unsigned long long* __restrict__ ctr) {
+            int merge_max, unsigned* tlow, unsigned long long* __restrict__ ctr) {
     extern __shared__ __align__(16) unsigned smem[];
     __shared__ long long s_unit;
     __shared__ int s_ctl[4];
@@ -786,7 +869,8 @@ __global__ void __launch_bounds__(256, TC_LARGE_MINB)
             const Unit U = small[u];
             const GraphView G = views[U.g];
             acc.to(unit_target(G, U));
-            warp_unit<PV>(G, U, wregion, wcnt, s_base, table_mode == 1, tlow, acc.hits, probes, staged);
+            warp_unit<PV, MERGE>(G, U, wregion, wcnt, s_base, table_mode == 1, merge_max, tlow, acc.hits,
+                                 probes, staged);
             if (lane == 0) {
                 atomicAdd(&s_work[0], 1ull);
                 atomicAdd(&s_work[2], (unsigned long long)(U.t1 - U.t0));
@@ -977,12 +1061,23 @@ size_t count_smem_bytes(bool pv, int threads, int unit_tasks) {
            sizeof(unsigned short) * (size_t)unit_tasks;
 }
 
+using CountKernel = void (*)(const GraphView*, const Unit*, int64_t, const Unit*, int64_t, int, int, int,
+                            unsigned*, unsigned long long*);
+
+// the count kernel instance for a launch: per-vertex or totals, with or
+// without the search path for short pivot rows
+CountKernel count_kernel(bool pv, bool merge) {
+    return pv ? (merge ? k_count<true, true> : k_count<true, false>)
+              : (merge ? k_count<false, true> : k_count<false, false>);
+}
+
 CountLaunch prepare_count(const UnitLists& L, const tc_tuning& t, bool pv) {
     CountLaunch c;
     c.threads = t.cta_threads;
     c.smem = count_smem_bytes(pv, c.threads, t.cta_unit_tasks);
     c.pv = pv;
-    auto kern = pv ? k_count<true> : k_count<false>;
+    c.merge = t.merge_max_outdeg > 0;
+    auto kern = count_kernel(pv, c.merge);
     TC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem));
     int per_sm = 0;
     TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, c.threads, c.smem));
@@ -996,9 +1091,9 @@ CountLaunch prepare_count(const UnitLists& L, const tc_tuning& t, bool pv) {
 void launch_count_raw(const CountLaunch& c, const GraphView* views_dev, const UnitLists& L,
                       const tc_tuning& t, unsigned long long* ctr, cudaStream_t st, unsigned* tlow) {
     if (L.nlarge + L.nsmall == 0) return;
-    auto kern = c.pv ? k_count<true> : k_count<false>;
+    auto kern = count_kernel(c.pv, c.merge);
     kern<<<c.grid, c.threads, c.smem, st>>>(views_dev, L.large, L.nlarge, L.small, L.nsmall,
-                                            t.slice_max, t.table_mode, tlow, ctr);
+                                            t.slice_max, t.table_mode, t.merge_max_outdeg, tlow, ctr);
     TC_LAUNCH_CHECK();
 }
 

@@ -453,6 +453,8 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
                 TC_CUDA(r);
                 method = ce < sm ? 1 : 2;
                 done = 2 * kSlice;
+                g->upload_probe_gbs[0] = 4.0 * kSlice / (ce * 1e6);
+                g->upload_probe_gbs[1] = 4.0 * kSlice / (sm * 1e6);
             }
             upload_i32(src_in + done, ms + done, hsrc.get() + done, P - done, method, st);
             upload_i32(dst_in, md, hdst.get(), P, method, st);

@@ -68,6 +68,7 @@ struct CountLaunch {
     int threads = 256;
     size_t smem = 0;
     bool pv = false;
+    bool merge = false;   // the instance with the search path for short pivot rows
 };
 // Sets the kernel's shared-memory attribute and sizes the persistent grid
 // (not a stream operation: call it outside stream capture).

@@ -39,7 +39,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("small_max_outdeg", ctypes.c_int32), ("warp_unit_tasks", ctypes.c_int32),
                 ("cta_unit_tasks", ctypes.c_int32), ("cta_threads", ctypes.c_int32),
                 ("slice_max", ctypes.c_int32), ("table_mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("merge_max_outdeg", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class GraphStats(ctypes.Structure):
@@ -116,7 +116,8 @@ class MemoryStats(ctypes.Structure):
 class TrianglesTiming(ctypes.Structure):
     _fields_ = [(f, ctypes.c_double) for f in ("wall_ms", "h2d_ms", "preprocess_ms", "count_ms",
                                                 "d2h_ms", "h2d_issue_ms")] + \
-               [("input_pinned", ctypes.c_int32), ("upload_method", ctypes.c_int32)]
+               [("input_pinned", ctypes.c_int32), ("upload_method", ctypes.c_int32),
+                ("ce_slice_gbs", ctypes.c_double), ("sm_slice_gbs", ctypes.c_double)]
 
 
 class TiledStats(ctypes.Structure):
@@ -588,6 +589,8 @@ def triangles_timing() -> dict:
     out = {f: float(getattr(t, f)) for f, _ in TrianglesTiming._fields_[:6]}
     out["input_pinned"] = bool(t.input_pinned)
     out["upload_method"] = {1: "copy engine", 2: "SM loads"}.get(int(t.upload_method), "none")
+    out["ce_slice_gbs"] = float(t.ce_slice_gbs)
+    out["sm_slice_gbs"] = float(t.sm_slice_gbs)
     return out
 
 

@@ -89,12 +89,14 @@ def test_batch_autotune_keeps_counts(tc):
     b = tc.Batch(graphs)
     t = b.autotune(reps=1)
     assert t.small_max_outdeg in (16, 64) and t.cta_threads in (128, 256)
+    assert t.merge_max_outdeg in (0, 16)
     assert b.count().cpu().numpy().tolist() == want
     # a second batch with the same profile reuses the cached choice
     b2 = tc.Batch(graphs)
     t2 = b2.autotune(reps=1)
-    assert (t2.small_max_outdeg, t2.warp_unit_tasks, t2.cta_unit_tasks, t2.cta_threads) == \
-           (t.small_max_outdeg, t.warp_unit_tasks, t.cta_unit_tasks, t.cta_threads)
+    assert (t2.small_max_outdeg, t2.warp_unit_tasks, t2.cta_unit_tasks, t2.cta_threads,
+            t2.merge_max_outdeg) == \
+           (t.small_max_outdeg, t.warp_unit_tasks, t.cta_unit_tasks, t.cta_threads, t.merge_max_outdeg)
     assert b2.count().cpu().numpy().tolist() == want
     for x in (b, b2):
         x.free()

@@ -209,10 +209,12 @@ TUNINGS = [
     dict(small_max_outdeg=1),                      # everything through the CTA kernel
     dict(small_max_outdeg=64, slice_max=64),       # pivots split into many slices
     dict(warp_unit_tasks=1, cta_unit_tasks=1),     # one task per unit
-    dict(cta_threads=1024, cta_unit_tasks=100000), # one unit per pivot, big CTAs
+    dict(cta_threads=256, cta_unit_tasks=100000),  # one unit per pivot (tasks capped at 8192)
     dict(cta_threads=64, slice_max=100),
     dict(table_mode=1),                            # hash tables only
     dict(table_mode=1, small_max_outdeg=1, slice_max=64),
+    dict(merge_max_outdeg=64),                     # every warp unit by search, no table
+    dict(merge_max_outdeg=8, small_max_outdeg=16, warp_unit_tasks=3),
 ]
 
 
