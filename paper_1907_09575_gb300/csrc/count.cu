@@ -44,18 +44,10 @@ constexpr int kEmpty = -1;
 #define TC_UNROLL 4
 #endif
 constexpr int kUnroll = TC_UNROLL;   // independent loads in flight per lane
-#ifndef TC_PV_WALK
-#define TC_PV_WALK 0           // per-vertex long walk: 0 checked rounds, 1 unchecked full rounds
-#endif
 #ifndef TC_PV_BRANCHLESS
 #define TC_PV_BRANCHLESS 1     // per-vertex bitmap probe: 1 computes the rank on every lane
 #endif
-#ifndef TC_PV_ATOM_LOOP
-#define TC_PV_ATOM_LOOP 0      // per-vertex long walk: 1 gathers a round's hits per lane, then loops
-#endif
-#ifndef TC_PV_PRED_RED
-#define TC_PV_PRED_RED 0       // per-hit shared counter add: 1 as one predicated red (no branch)
-#endif
+
 // warp unit table region: 128 hash slots, or a 128-word bitmap (4095 labels
 // and the guard bit)
 // plus its 128 16-bit rank prefixes
@@ -131,14 +123,6 @@ struct BitTab {
         const unsigned d = offset(k);
         return (bm[d >> 5] >> (d & 31)) & 1u;
     }
-    // the rank and the hit bit of a probe (rank meaningful only on a hit)
-    __device__ __forceinline__ int rank_hit(int k, unsigned& h) const {
-        const unsigned d = offset(k);
-        const unsigned w = bm[d >> 5];
-        const unsigned b = d & 31;
-        h = (w >> b) & 1u;
-        return (int)pre[d >> 5] + __popc(w & ((1u << b) - 1u));
-    }
     // membership and rank without a branch on the membership: the rank is
     // read for every probe (the guard bit's word has a prefix too), and only
     // the credit is predicated on the hit
@@ -149,13 +133,7 @@ struct BitTab {
         const unsigned h = (w >> b) & 1u;
         const int r = (int)pre[d >> 5] + __popc(w & ((1u << b) - 1u));
         mine += h;
-#if TC_PV_PRED_RED
-        const unsigned a = (unsigned)__cvta_generic_to_shared(&cnt[r]);
-        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\t@p red.shared.add.u32 [%0], 1;\n\t}"
-                     ::"r"(a), "r"(h) : "memory");
-#else
         if (h) atomicAdd(&cnt[r], 1u);
-#endif
     }
     // hit counters by rank (rank < slice <= 4096): one word each, so hits on
     // neighbouring entries never share an atomic's word
@@ -232,32 +210,6 @@ __device__ __forceinline__ unsigned hash_buckets(int dp) {
 }
 
 
-// A round's probes, then each lane's hits credited in a loop: a warp issues
-// as many counter adds as its busiest lane has hits (about 2.6 for 4 probes
-// a lane at a 1-in-5 hit rate) instead of one per probe step.
-template <class Tab>
-__device__ __forceinline__ void probe_round_credit(const Tab& T, const int (&k)[kUnroll], unsigned* cnt,
-                                                   unsigned& mine) {
-    int r[kUnroll];
-    unsigned hm = 0;
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-        unsigned h;
-        r[u] = T.rank_hit(k[u], h);
-        hm |= h << u;
-    }
-    mine += __popc(hm);
-    while (hm) {
-        const int u = __ffs(hm) - 1;
-        hm &= hm - 1u;
-        int rr = r[0];
-#pragma unroll
-        for (int q = 1; q < kUnroll; ++q)
-            if (u == q) rr = r[q];
-        atomicAdd(&cnt[rr], 1u);
-    }
-}
-
 template <class Tab>
 struct has_probe_credit {
     template <class U>
@@ -298,40 +250,7 @@ __device__ __forceinline__ unsigned warp_walk_tail(int64_t st, int L, const int3
     const int lane = threadIdx.x & 31;
     const int32_t* __restrict__ p = adj + st + lane;
     unsigned mine = 0;
-    if constexpr (PV && TC_PV_WALK == 1) {
-        // full rounds unchecked, each loading the next full round before it
-        // probes; then one checked round for the rest
-        constexpr int R = 32 * kUnroll;
-        const int full = L - L % R;
-        int q0 = 0;
-        if (full > 0) {
-            int k[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) k[u] = __ldg(p + 32 * u);
-            for (; q0 + R < full; q0 += R) {
-                int kn[kUnroll];
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u) kn[u] = __ldg(p + q0 + R + 32 * u);
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u) probe_one<PV>(T, k[u], cnt, mine);
-#pragma unroll
-                for (int u = 0; u < kUnroll; ++u) k[u] = kn[u];
-            }
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) probe_one<PV>(T, k[u], cnt, mine);
-            q0 = full;
-        }
-        if (q0 < L) {
-            int k[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) k[u] = (q0 + 32 * u + lane < L) ? __ldg(p + q0 + 32 * u) : -1;
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u)
-                if (k[u] >= 0) probe_one<PV>(T, k[u], cnt, mine);
-        }
-        hits += mine;
-        return __reduce_add_sync(0xffffffffu, mine);
-    } else if constexpr (PV) {
+    if constexpr (PV) {
         int k[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) k[u] = (32 * u + lane < L) ? __ldg(p + 32 * u) : -1;
@@ -340,13 +259,9 @@ __device__ __forceinline__ unsigned warp_walk_tail(int64_t st, int L, const int3
             int kn[kUnroll];
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) kn[u] = (q1 + 32 * u + lane < L) ? __ldg(p + q1 + 32 * u) : -1;
-            if constexpr (TC_PV_ATOM_LOOP && has_probe_credit<Tab>::value) {
-                probe_round_credit(T, k, cnt, mine);   // k < 0 lands on the clear guard bit
-            } else {
 #pragma unroll
-                for (int u = 0; u < kUnroll; ++u)
-                    if (k[u] >= 0) probe_one<PV>(T, k[u], cnt, mine);
-            }
+            for (int u = 0; u < kUnroll; ++u)
+                if (k[u] >= 0) probe_one<PV>(T, k[u], cnt, mine);
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) k[u] = kn[u];
         }

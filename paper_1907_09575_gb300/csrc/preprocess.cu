@@ -4,9 +4,11 @@
 //   a2 unique         up to 2^26 pairs: keys inserted into a device hash set
 //                     (open addressing, load <= 1/2) whose compacted slots
 //                     are E, in no particular order (a5 sorts them).  Larger
-//                     inputs: LSD radix sort, first of each run kept -- the
-//                     set's random atomics into a table of 2^31 slots ran
-//                     slower than the sort's passes (measured at 2^30 pairs).
+//                     inputs: LSD radix sort whose digit count and first pass
+//                     make the canonical keys from the pairs, first of each
+//                     run kept -- the set's random atomics into a table of
+//                     2^31 slots ran slower than the sort's passes (measured
+//                     at 2^30 pairs).
 //   a3 degrees        d(v) counted when a key enters the set / from the
 //                     unique runs
 //   a4 relabel        stable sort of (d(v) << b | v) on the degree bits: the
@@ -26,6 +28,11 @@ namespace tc {
 namespace {
 
 constexpr int kT = 256;
+
+#ifndef TC_DEGREE_COUNTING
+#define TC_DEGREE_COUNTING 0   // a4: 0 radix sort on the degree bits; 1 counting pass + heavy tail
+#endif
+constexpr int kHeavy = 255;    // degrees clipped here by the counting pass
 
 constexpr uint64_t kEmptyKey = ~0ull;   // no key: keys use 2b <= 62 bits
 constexpr int64_t kHashDedupMaxPairs = 1ll << 26;   // table of at most 2^27 slots (1 GB)
@@ -132,23 +139,6 @@ __device__ __forceinline__ void warp_add_sorted(int32_t* counter, int32_t v, boo
     }
 }
 
-__global__ void k_canon(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
-                        int64_t P, int64_t n, int bits, uint64_t sentinel,
-                        uint64_t* __restrict__ keys, int* __restrict__ err) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int32_t a = src[e], b = dst[e];
-        uint64_t k = sentinel;
-        if (a < 0 || b < 0 || (int64_t)a >= n || (int64_t)b >= n) {
-            atomicOr(err, 1);
-        } else if (a != b) {
-            uint64_t lo = (uint64_t)min(a, b), hi = (uint64_t)max(a, b);
-            k = (lo << bits) | hi;
-        }
-        keys[e] = k;
-    }
-}
-
 __global__ void k_unique_flags(const uint64_t* __restrict__ keys, int64_t P, uint64_t sentinel,
                                int32_t* __restrict__ flags) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P;
@@ -175,14 +165,43 @@ __global__ void k_unique_compact(const uint64_t* __restrict__ keys, const int32_
     }
 }
 
+// out[0] = max of x; out[2] += the entries >= kHeavy
 __global__ void k_max_i32(const int32_t* __restrict__ x, int64_t n, int* __restrict__ out) {
-    int mx = 0;
+    int mx = 0, heavy = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        mx = max(mx, x[v]);
+        heavy += x[v] >= kHeavy;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        heavy += __shfl_xor_sync(0xffffffffu, heavy, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(out, mx);
+        if (heavy) atomicAdd(out + 2, heavy);
+    }
+}
+
+// the counting pass's keys: degree clipped to kHeavy, then the id
+__global__ void k_degree_keys_clipped(const int32_t* __restrict__ deg, int64_t n, int bits,
+                                      uint64_t* __restrict__ keys) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x)
-        mx = max(mx, x[v]);
-#pragma unroll
-    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
+        keys[v] = ((uint64_t)(uint32_t)min(deg[v], kHeavy) << bits) | (uint64_t)v;
+}
+
+// the heavy tail (the last h keys of the counting pass, ids in order) with
+// their full degrees
+__global__ void k_heavy_keys(const uint64_t* __restrict__ sorted, int64_t n, int64_t h, int bits,
+                             const int32_t* __restrict__ deg, uint64_t* __restrict__ out) {
+    const uint64_t mask = (1ull << bits) - 1ull;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < h;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t v = sorted[n - h + q] & mask;
+        out[q] = ((uint64_t)(uint32_t)deg[v] << bits) | v;
+    }
 }
 
 __global__ void k_degree_keys(const int32_t* __restrict__ deg, int64_t n, int bits,
@@ -201,6 +220,18 @@ __global__ void k_perm(const uint64_t* __restrict__ sorted, int64_t n, int bits,
         const uint64_t k = sorted[r];
         perm[k & mask] = (int32_t)r;
         degn[r] = (int32_t)(k >> bits);
+    }
+}
+
+// the same for sorted keys whose ranks start at r0
+__global__ void k_perm_at(const uint64_t* __restrict__ sorted, int64_t count, int64_t r0, int bits,
+                          int32_t* __restrict__ perm, int32_t* __restrict__ degn) {
+    const uint64_t mask = (1ull << bits) - 1ull;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = sorted[q];
+        perm[k & mask] = (int32_t)(r0 + q);
+        degn[r0 + q] = (int32_t)(k >> bits);
     }
 }
 
@@ -431,34 +462,47 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
         const int32_t* md = mapped_host(dst_in);
         if (ms && md) {
             // Page-locked pairs: the copy engine and SM loads over the link
-            // reach different rates on different boxes (memory placement);
-            // a large upload times one slice each way and sends the rest by
-            // the faster.  The slices are parts of the upload.
+            // reach different rates on different boxes (memory placement,
+            // other traffic on the host side), and together no more than
+            // the link gives (measured: running both at once, split by their
+            // rates, was slower than the faster alone).  A large upload times
+            // one slice each way and sends the rest by the faster.  The
+            // slices are parts of the upload.
             constexpr int64_t kSlice = 32ll << 20;   // int32: 128 MB
-            int method = 2;
-            int64_t done = 0;
             if (P >= 4 * kSlice) {
                 cudaEvent_t e[3] = {};
-                for (auto& x : e) TC_CUDA(cudaEventCreate(&x));
-                TC_CUDA(cudaEventRecord(e[0], st));
-                upload_i32(src_in, ms, hsrc.get(), kSlice, 1, st);
-                TC_CUDA(cudaEventRecord(e[1], st));
-                upload_i32(src_in + kSlice, ms + kSlice, hsrc.get() + kSlice, kSlice, 2, st);
-                TC_CUDA(cudaEventRecord(e[2], st));
-                float ce = 0.f, sm = 0.f;
-                cudaError_t r = cudaEventSynchronize(e[2]);
-                if (r == cudaSuccess) r = cudaEventElapsedTime(&ce, e[0], e[1]);
-                if (r == cudaSuccess) r = cudaEventElapsedTime(&sm, e[1], e[2]);
-                for (auto& x : e) cudaEventDestroy(x);
-                TC_CUDA(r);
-                method = ce < sm ? 1 : 2;
-                done = 2 * kSlice;
-                g->upload_probe_gbs[0] = 4.0 * kSlice / (ce * 1e6);
-                g->upload_probe_gbs[1] = 4.0 * kSlice / (sm * 1e6);
+                auto cleanup = [&]() {
+                    for (auto& x : e)
+                        if (x) cudaEventDestroy(x);
+                };
+                try {
+                    for (auto& x : e) TC_CUDA(cudaEventCreate(&x));
+                    TC_CUDA(cudaEventRecord(e[0], st));
+                    upload_i32(src_in, ms, hsrc.get(), kSlice, 1, st);
+                    TC_CUDA(cudaEventRecord(e[1], st));
+                    upload_i32(src_in + kSlice, ms + kSlice, hsrc.get() + kSlice, kSlice, 2, st);
+                    TC_CUDA(cudaEventRecord(e[2], st));
+                    float ce = 0.f, sm = 0.f;
+                    TC_CUDA(cudaEventSynchronize(e[2]));
+                    TC_CUDA(cudaEventElapsedTime(&ce, e[0], e[1]));
+                    TC_CUDA(cudaEventElapsedTime(&sm, e[1], e[2]));
+                    g->upload_probe_gbs[0] = 4.0 * kSlice / (std::max(ce, 1e-6f) * 1e6);
+                    g->upload_probe_gbs[1] = 4.0 * kSlice / (std::max(sm, 1e-6f) * 1e6);
+                    const int method = ce < sm ? 1 : 2;
+                    upload_i32(src_in + 2 * kSlice, ms + 2 * kSlice, hsrc.get() + 2 * kSlice, P - 2 * kSlice,
+                               method, st);
+                    upload_i32(dst_in, md, hdst.get(), P, method, st);
+                    g->upload_method = method;
+                } catch (...) {
+                    cleanup();
+                    throw;
+                }
+                cleanup();
+            } else {
+                upload_i32(src_in, ms, hsrc.get(), P, 2, st);
+                upload_i32(dst_in, md, hdst.get(), P, 2, st);
+                g->upload_method = 2;
             }
-            upload_i32(src_in + done, ms + done, hsrc.get() + done, P - done, method, st);
-            upload_i32(dst_in, md, hdst.get(), P, method, st);
-            g->upload_method = method;
         } else {
             TC_CUDA(cudaMemcpyAsync(hsrc.get(), src_in, sizeof(int32_t) * P, cudaMemcpyHostToDevice, st));
             TC_CUDA(cudaMemcpyAsync(hdst.get(), dst_in, sizeof(int32_t) * P, cudaMemcpyHostToDevice, st));
@@ -471,7 +515,7 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
     }
     if (g->ev_uploaded) TC_CUDA(cudaEventRecord(g->ev_uploaded, st));
 
-    Buf<int> scal(al, 8);   // [0] err, [1] max degree, [2] max out-degree
+    Buf<int> scal(al, 8);   // [0] err, [1] max degree, [2] max out-degree, [3] heavy vertices
     TC_CUDA(cudaMemsetAsync(scal.get(), 0, 8 * sizeof(int), st));
     Buf<int64_t> vpre;
     if (num_comps > 0) {
@@ -518,24 +562,21 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
         }
         TC_LAUNCH_CHECK();
     } else if (P > 0) {
-        // canonical keys, radix sorted, first of each run kept
+        // canonical keys, radix sorted, first of each run kept: the digit
+        // count and the first pass make each key from its pair (no key array
+        // is written first)
         const uint64_t sentinel = (bits * 2 >= 64) ? ~0ull : ((1ull << (2 * bits)) - 1ull);
         ab = Buf<uint64_t>(al, (size_t)P);
         alt = ab.get();
-        {
-            Prof prof_("k_canon", st);
-            k_canon<<<grid_for(P, kT, G), kT, 0, st>>>(src, dst, P, n, bits, sentinel, keys, scal.get());
-        }
-        TC_LAUNCH_CHECK();
         if (num_comps > 0) {
             Prof prof_("k_check_comp", st);
             k_check_comp<<<grid_for(P, kT, G), kT, 0, st>>>(src, dst, P, vpre.get(), num_comps, scal.get());
         }
         TC_LAUNCH_CHECK();
+        // ids outside [0, n) became sentinels; the error is read at the next sync
+        radix_sort_pairs(src, dst, P, n, bits, sentinel, &keys, &alt, al, st, scal.get());
         hsrc.release();
         hdst.release();
-        // ids outside [0, n) became sentinels; the error is read at the next sync
-        radix_sort_u64(&keys, &alt, P, 0, 2 * bits, al, st, scal.get());
         {
             Buf<int32_t> fl(al, (size_t)P);
             Buf<int64_t> pos(al, (size_t)P);
@@ -554,22 +595,23 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
         }
         std::swap(keys, alt);  // E now in `keys`
     }
-    // one synchronisation for: errors so far, m, max degree
-    int maxdeg = 0;
+    // one synchronisation for: errors so far, m, max degree, heavy vertices
+    int maxdeg = 0, nheavy = 0;
     {
         if (n > 0) {
             Prof prof_("k_max_i32", st);
-            k_max_i32<<<grid_for(n, kT, G), kT, 0, st>>>(deg.get(), n, scal.get() + 1);
+            k_max_i32<<<grid_for(n, kT, G), kT, 0, st>>>(deg.get(), n, scal.get() + 1);   // [1], [3]
         }
         TC_LAUNCH_CHECK();
-        int hs[2] = {0, 0};
-        TC_CUDA(cudaMemcpyAsync(hs, scal.get(), 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        int hs[4] = {0, 0, 0, 0};
+        TC_CUDA(cudaMemcpyAsync(hs, scal.get(), 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
         if (P > 0) TC_CUDA(cudaMemcpyAsync(&m, tot.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         TC_CUDA(cudaStreamSynchronize(st));
         if (hs[0] & 1) TC_FAIL(TC_EINVAL, "tc_preprocess: a vertex id lies outside [0, n)");
         if (hs[0] & 2) TC_FAIL(TC_EINVAL, "tc_preprocess_components: a pair joins two components");
         if (hs[0] & 4) TC_FAIL(TC_ETIMEOUT, "tc_preprocess: a sort look-back wait ran past its bound");
         maxdeg = hs[1];
+        nheavy = hs[3];
     }
     g->m = m;
     g->stats.m = m;
@@ -616,18 +658,60 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
         Buf<uint64_t> dk(al, (size_t)n), da(al, (size_t)n);
         uint64_t* dkeys = dk.get();
         uint64_t* dalt = da.get();
-        {
-            Prof prof_("k_degree_keys", st);
-            k_degree_keys<<<grid_for(n, kT, G), kT, 0, st>>>(deg.get(), n, bits, dkeys);
+        if (TC_DEGREE_COUNTING) {
+            // the counting sort of Section 5.3 for degrees below kHeavy (one
+            // stable pass), the heavy tail sorted on its full degrees
+            {
+                Prof prof_("k_degree_keys", st);
+                k_degree_keys_clipped<<<grid_for(n, kT, G), kT, 0, st>>>(deg.get(), n, bits, dkeys);
+            }
+            TC_LAUNCH_CHECK();
+            radix_sort_u64(&dkeys, &dalt, n, bits, bits + 8, al, st, scal.get());
+            // the heavy tail's keys are read (degrees by original id) before
+            // k_perm overwrites deg with the degrees in rank order
+            Buf<uint64_t> hk, ha;
+            uint64_t* hkeys = nullptr;
+            uint64_t* halt = nullptr;
+            if (nheavy > 0) {
+                hk = Buf<uint64_t>(al, (size_t)nheavy);
+                ha = Buf<uint64_t>(al, (size_t)nheavy);
+                hkeys = hk.get();
+                halt = ha.get();
+                {
+                    Prof prof_("k_heavy_keys", st);
+                    k_heavy_keys<<<grid_for(nheavy, kT, G), kT, 0, st>>>(dkeys, n, nheavy, bits, deg.get(), hkeys);
+                }
+                TC_LAUNCH_CHECK();
+            }
+            {
+                Prof prof_("k_perm", st);
+                k_perm<<<grid_for(n - nheavy, kT, G), kT, 0, st>>>(dkeys, n - nheavy, bits, g->perm, deg.get());
+            }
+            TC_LAUNCH_CHECK();
+            if (nheavy > 0) {
+                const int dbits = ceil_log2_u64((uint64_t)maxdeg + 1);
+                radix_sort_u64(&hkeys, &halt, nheavy, bits, bits + dbits, al, st, scal.get());
+                {
+                    Prof prof_("k_perm", st);
+                    k_perm_at<<<grid_for(nheavy, kT, G), kT, 0, st>>>(hkeys, nheavy, n - nheavy, bits, g->perm,
+                                                                      deg.get());
+                }
+                TC_LAUNCH_CHECK();
+            }
+        } else {
+            {
+                Prof prof_("k_degree_keys", st);
+                k_degree_keys<<<grid_for(n, kT, G), kT, 0, st>>>(deg.get(), n, bits, dkeys);
+            }
+            TC_LAUNCH_CHECK();
+            int dbits = ceil_log2_u64((uint64_t)maxdeg + 1);
+            radix_sort_u64(&dkeys, &dalt, n, bits, bits + dbits, al, st, scal.get());
+            {
+                Prof prof_("k_perm", st);
+                k_perm<<<grid_for(n, kT, G), kT, 0, st>>>(dkeys, n, bits, g->perm, deg.get());
+            }
+            TC_LAUNCH_CHECK();
         }
-        TC_LAUNCH_CHECK();
-        int dbits = ceil_log2_u64((uint64_t)maxdeg + 1);
-        radix_sort_u64(&dkeys, &dalt, n, bits, bits + dbits, al, st, scal.get());
-        {
-            Prof prof_("k_perm", st);
-            k_perm<<<grid_for(n, kT, G), kT, 0, st>>>(dkeys, n, bits, g->perm, deg.get());
-        }
-        TC_LAUNCH_CHECK();
     }
     g->stats.max_deg = maxdeg;
     if (num_comps > 0 && n > 0) {
