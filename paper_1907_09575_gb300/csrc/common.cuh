@@ -238,6 +238,8 @@ struct GraphView {
     int32_t off64;
     int32_t jbase;                // label of local pivot 0 (tiles of a host-resident
                                   // graph index pivots from their block's start)
+    int32_t i0, i1;               // tiles: the rows counted by this launch ...
+    int64_t tail_shift;           // ... whose entries start this far into adj
 };
 
 // Device counters of one count: queue heads, the total, and work done by the

@@ -82,6 +82,15 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
     return v;
 }
 
+// The rows a launch counts and where their tails sit: all rows at their
+// place for a device-resident graph; for one tile of a host-resident graph
+// the rows [i0, i1) of its row block, whose entries start `shift` entries
+// into the tile's row buffer.
+struct TaskWindow {
+    int i0, i1;
+    int64_t shift;
+};
+
 // bits [lo, hi) of a 32-bit mask, 0 <= lo <= hi <= 32
 __device__ __forceinline__ unsigned bit_range(int lo, int hi) {
     const unsigned up = (hi >= 32) ? 0xffffffffu : ((1u << hi) - 1u);
@@ -319,12 +328,13 @@ __device__ __forceinline__ void credit_task(unsigned long long* tnew, unsigned* 
 // steps, takes its hits from their popcounts over its positions at the end.
 // Each task's hits go once to tnew[i]; per-entry hits to the counters cnt.
 // ---------------------------------------------------------------------------
-template <bool PV, class Tab>
+template <bool PV, bool WIN, class Tab>
 __device__ __forceinline__ void warp_probe_group(const Task* __restrict__ tasks, int64_t tb, int64_t t1,
                                                  const int32_t* __restrict__ adj, const Tab& T,
                                                  unsigned* cnt, unsigned long long* tnew, unsigned* tlow,
                                                  int64_t* s_base, int64_t t0, unsigned short* defer,
-                                                 int* ndefer, uint64_t& hits, uint64_t& probes) {
+                                                 int* ndefer, uint64_t& hits, uint64_t& probes,
+                                                 const TaskWindow& win) {
     const int lane = threadIdx.x & 31;
     const int64_t t = tb + lane;
     const bool valid = t < t1;
@@ -335,6 +345,12 @@ __device__ __forceinline__ void warp_probe_group(const Task* __restrict__ tasks,
         start = tk.start;
         len = tk.len;
         i = tk.i;
+        if (WIN) {
+            // a tile of a host-resident graph: rows outside its block wait
+            // for another tile; tails are read from the tile's row buffer
+            if (i < win.i0 || i >= win.i1) len = 0;
+            start -= win.shift;
+        }
     }
     unsigned c = 0;
     const unsigned le = (2u << lane) - 1u;   // bits 0..lane
@@ -444,7 +460,7 @@ struct GraphAcc {
 // Warp unit: a pivot with |U_j| <= 64 processed by one warp with a private
 // table (a bitmap of <= 4095 labels, or 128 hash slots).
 // ---------------------------------------------------------------------------
-template <bool PV, bool MERGE>
+template <bool PV, bool MERGE, bool WIN>
 __device__ __forceinline__ void warp_unit(const GraphView& G, const Unit& U, unsigned* region,
                                           unsigned* cnt, int64_t* s_base, bool hash_only, int merge_max,
                                           unsigned* tlow, uint64_t& hits, uint64_t& probes, uint64_t& staged) {
@@ -465,8 +481,8 @@ __device__ __forceinline__ void warp_unit(const GraphView& G, const Unit& U, uns
         __syncwarp();
         const SearchTab T{piv, dp, lo, hi};
         for (int64_t tb = U.t0; tb < U.t1; tb += 32)
-            warp_probe_group<PV>(G.tasks, tb, U.t1, G.adj, T, cnt, G.tnew, tlow, s_base, U.t0, nullptr,
-                                 nullptr, uh, probes);
+            warp_probe_group<PV, WIN>(G.tasks, tb, U.t1, G.adj, T, cnt, G.tnew, tlow, s_base, U.t0, nullptr,
+                                      nullptr, uh, probes, TaskWindow{G.i0, G.i1, G.tail_shift});
         __syncwarp();
         if (PV) {
             if (lane < dp) {
@@ -506,8 +522,8 @@ __device__ __forceinline__ void warp_unit(const GraphView& G, const Unit& U, uns
         __syncwarp();
         const BitTab T{region, pre, lo, hi};
         for (int64_t tb = U.t0; tb < U.t1; tb += 32)
-            warp_probe_group<PV>(G.tasks, tb, U.t1, G.adj, T, cnt, G.tnew, tlow, s_base, U.t0, nullptr,
-                                 nullptr, uh, probes);
+            warp_probe_group<PV, WIN>(G.tasks, tb, U.t1, G.adj, T, cnt, G.tnew, tlow, s_base, U.t0, nullptr,
+                                      nullptr, uh, probes, TaskWindow{G.i0, G.i1, G.tail_shift});
         __syncwarp();
         if (PV) {
             if (lane < dp) {
@@ -529,8 +545,8 @@ __device__ __forceinline__ void warp_unit(const GraphView& G, const Unit& U, uns
         __syncwarp();
         const HashTab T{tab, bmask, lo, hi};
         for (int64_t tb = U.t0; tb < U.t1; tb += 32)
-            warp_probe_group<PV>(G.tasks, tb, U.t1, G.adj, T, cnt, G.tnew, tlow, s_base, U.t0, nullptr,
-                                 nullptr, uh, probes);
+            warp_probe_group<PV, WIN>(G.tasks, tb, U.t1, G.adj, T, cnt, G.tnew, tlow, s_base, U.t0, nullptr,
+                                      nullptr, uh, probes, TaskWindow{G.i0, G.i1, G.tail_shift});
         __syncwarp();
         if (PV)
             for (int s = lane; s < kSmallTable; s += 32) {
@@ -554,7 +570,7 @@ __device__ __forceinline__ void warp_unit(const GraphView& G, const Unit& U, uns
 // time, with later tasks' records already loading and the next tail
 // prefetched into L2 while the current tail is walked.
 // ---------------------------------------------------------------------------
-template <bool PV, class Tab>
+template <bool PV, bool WIN, class Tab>
 __device__ __forceinline__ void cta_probe_unit(const GraphView& G, const Unit& U, const Tab& T,
                                                unsigned* cnt, int* s_ctl, int64_t* s_base,
                                                unsigned short* s_long, unsigned* tlow, uint64_t& uh,
@@ -569,8 +585,8 @@ __device__ __forceinline__ void cta_probe_unit(const GraphView& G, const Unit& U
         g = __shfl_sync(0xffffffffu, g, 0);
         const int64_t tb = U.t0 + (int64_t)g * 32;
         if (tb >= U.t1) break;
-        warp_probe_group<PV>(tasks, tb, U.t1, adj, T, cnt, G.tnew, tlow, s_base, U.t0, s_long, &s_ctl[1],
-                             uh, probes);
+        warp_probe_group<PV, WIN>(tasks, tb, U.t1, adj, T, cnt, G.tnew, tlow, s_base, U.t0, s_long,
+                                  &s_ctl[1], uh, probes, TaskWindow{G.i0, G.i1, G.tail_shift});
     }
     __syncthreads();
     const int nlong = s_ctl[1];
@@ -579,10 +595,15 @@ __device__ __forceinline__ void cta_probe_unit(const GraphView& G, const Unit& U
         if (lane == 0) v = atomicAdd(&s_ctl[2], 1);
         return __shfl_sync(0xffffffffu, v, 0);
     };
+    // deferred tasks passed the window in phase A; only their tails move
+    const int64_t shift = WIN ? G.tail_shift : 0;
     auto record = [&](int x) {
         Task t;
         t.len = 0;
-        if (x < nlong) t = tasks[U.t0 + s_long[x]];
+        if (x < nlong) {
+            t = tasks[U.t0 + s_long[x]];
+            t.start -= shift;
+        }
         return t;
     };
     // the next task's tail is prefetched into L2 while this one is walked
@@ -611,13 +632,17 @@ __device__ __forceinline__ void cta_probe_unit(const GraphView& G, const Unit& U
         int x = pop();
         Task cur;
         cur.len = 0;
-        if (x < nlong) cur = tasks[U.t0 + s_long[x]];
+        if (x < nlong) {
+            cur = tasks[U.t0 + s_long[x]];
+            cur.start -= shift;
+        }
         while (x < nlong) {
             const int xn = pop();
             Task nxt;
             nxt.len = 0;
             if (xn < nlong) {
                 nxt = tasks[U.t0 + s_long[xn]];
+                nxt.start -= shift;
                 if (32 * lane < nxt.len)
                     asm volatile("prefetch.global.L2 [%0];" ::"l"(adj + nxt.start + 32 * lane));
             }
@@ -630,7 +655,7 @@ __device__ __forceinline__ void cta_probe_unit(const GraphView& G, const Unit& U
     }
 }
 
-template <bool PV>
+template <bool PV, bool WIN>
 __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int slice_max,
                                          unsigned* region, unsigned* cnt, int* s_ctl,
                                          int64_t* s_base, unsigned short* s_long,
@@ -676,7 +701,7 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
             __syncthreads();
         }
         const BitTab T{region, pre, lo, hi};
-        cta_probe_unit<PV>(G, U, T, cnt, s_ctl, s_base, s_long, tlow, uh, probes);
+        cta_probe_unit<PV, WIN>(G, U, T, cnt, s_ctl, s_base, s_long, tlow, uh, probes);
         __syncthreads();
         if (PV)
             for (int r = threadIdx.x; r < dp; r += blockDim.x) {
@@ -692,7 +717,7 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
         for (int q = threadIdx.x; q < dp; q += blockDim.x) hash_insert(tab, bmask, G.adj[rb + q]);
         __syncthreads();
         const HashTab T{tab, bmask, lo, hi};
-        cta_probe_unit<PV>(G, U, T, cnt, s_ctl, s_base, s_long, tlow, uh, probes);
+        cta_probe_unit<PV, WIN>(G, U, T, cnt, s_ctl, s_base, s_long, tlow, uh, probes);
         __syncthreads();
         if (PV)
             for (int s = threadIdx.x; s < 4 * (int)buckets; s += blockDim.x) {
@@ -723,7 +748,7 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
 // (kRegionWords words; warp units use 192-word slices of it) | hit counters
 // (PV: kRegionWords/2 words) | long-task queue (unit_tasks x 16 bit).
 // ---------------------------------------------------------------------------
-template <bool PV, bool MERGE>
+template <bool PV, bool MERGE, bool WIN>
 __global__ void __launch_bounds__(256, TC_LARGE_MINB)
     k_count(const GraphView* __restrict__ views, const Unit* __restrict__ large, int64_t nlarge,
             const Unit* __restrict__ small, int64_t nsmall, int slice_max, int table_mode,
@@ -757,7 +782,7 @@ __global__ void __launch_bounds__(256, TC_LARGE_MINB)
         const Unit U = large[u];
         const GraphView G = views[U.g];
         acc.to(unit_target(G, U));
-        cta_unit<PV>(G, U, slice_max, region, cnt, s_ctl, s_base, s_long, s_wsum, s_red,
+        cta_unit<PV, WIN>(G, U, slice_max, region, cnt, s_ctl, s_base, s_long, s_wsum, s_red,
                      table_mode == 1, tlow, acc.hits, probes);
         if (threadIdx.x == 0) {
             s_work[1] += 1;
@@ -784,7 +809,7 @@ __global__ void __launch_bounds__(256, TC_LARGE_MINB)
             const Unit U = small[u];
             const GraphView G = views[U.g];
             acc.to(unit_target(G, U));
-            warp_unit<PV, MERGE>(G, U, wregion, wcnt, s_base, table_mode == 1, merge_max, tlow, acc.hits,
+            warp_unit<PV, MERGE, WIN>(G, U, wregion, wcnt, s_base, table_mode == 1, merge_max, tlow, acc.hits,
                                  probes, staged);
             if (lane == 0) {
                 atomicAdd(&s_work[0], 1ull);
@@ -980,19 +1005,22 @@ using CountKernel = void (*)(const GraphView*, const Unit*, int64_t, const Unit*
                             unsigned*, unsigned long long*);
 
 // the count kernel instance for a launch: per-vertex or totals, with or
-// without the search path for short pivot rows
-CountKernel count_kernel(bool pv, bool merge) {
-    return pv ? (merge ? k_count<true, true> : k_count<true, false>)
-              : (merge ? k_count<false, true> : k_count<false, false>);
+// without the search path for short pivot rows, or the instance that counts
+// one tile of a host-resident graph (a window of rows)
+CountKernel count_kernel(bool pv, bool merge, bool win) {
+    if (win) return pv ? k_count<true, false, true> : k_count<false, false, true>;
+    return pv ? (merge ? k_count<true, true, false> : k_count<true, false, false>)
+              : (merge ? k_count<false, true, false> : k_count<false, false, false>);
 }
 
-CountLaunch prepare_count(const UnitLists& L, const tc_tuning& t, bool pv) {
+CountLaunch prepare_count(const UnitLists& L, const tc_tuning& t, bool pv, bool win) {
     CountLaunch c;
     c.threads = t.cta_threads;
     c.smem = count_smem_bytes(pv, c.threads, t.cta_unit_tasks);
     c.pv = pv;
-    c.merge = t.merge_max_outdeg > 0;
-    auto kern = count_kernel(pv, c.merge);
+    c.merge = t.merge_max_outdeg > 0 && !win;
+    c.win = win;
+    auto kern = count_kernel(pv, c.merge, c.win);
     TC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem));
     int per_sm = 0;
     TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, c.threads, c.smem));
@@ -1006,16 +1034,16 @@ CountLaunch prepare_count(const UnitLists& L, const tc_tuning& t, bool pv) {
 void launch_count_raw(const CountLaunch& c, const GraphView* views_dev, const UnitLists& L,
                       const tc_tuning& t, unsigned long long* ctr, cudaStream_t st, unsigned* tlow) {
     if (L.nlarge + L.nsmall == 0) return;
-    auto kern = count_kernel(c.pv, c.merge);
+    auto kern = count_kernel(c.pv, c.merge, c.win);
     kern<<<c.grid, c.threads, c.smem, st>>>(views_dev, L.large, L.nlarge, L.small, L.nsmall,
                                             t.slice_max, t.table_mode, t.merge_max_outdeg, tlow, ctr);
     TC_LAUNCH_CHECK();
 }
 
 void launch_count(const GraphView* views_dev, const UnitLists& L, const tc_tuning& t, bool pv,
-                  unsigned long long* ctr, cudaStream_t st, bool profile, unsigned* tlow) {
+                  unsigned long long* ctr, cudaStream_t st, bool profile, unsigned* tlow, bool win) {
     if (L.nlarge + L.nsmall == 0) return;
-    const CountLaunch c = prepare_count(L, t, pv);
+    const CountLaunch c = prepare_count(L, t, pv, win);
     if (profile) {
         Prof prof_("k_count", st);
         launch_count_raw(c, views_dev, L, t, ctr, st, tlow);

@@ -11,8 +11,10 @@
 //                     at 2^30 pairs).
 //   a3 degrees        d(v) counted when a key enters the set / from the
 //                     unique runs
-//   a4 relabel        stable sort of (d(v) << b | v) on the degree bits: the
-//                     rank is the new label (non-decreasing degree, ties by id)
+//   a4 relabel        rank by (d(v), v): the counting sort of Section 5.3 as
+//                     one stable pass on the degree clipped at 255 (nearly
+//                     every vertex), the vertices at or above it then sorted
+//                     on their full degree; the rank is the new label
 //   a5 orient + CSR   (min, max) of the new labels, sorted -> U rows ascending
 //   a6 tasks + units  <j,i,k> tasks grouped by pivot j, then work units
 //
@@ -30,7 +32,7 @@ namespace {
 constexpr int kT = 256;
 
 #ifndef TC_DEGREE_COUNTING
-#define TC_DEGREE_COUNTING 0   // a4: 0 radix sort on the degree bits; 1 counting pass + heavy tail
+#define TC_DEGREE_COUNTING 1   // a4: 1 counting pass + heavy tail (Section 5.3); 0 radix on the degree bits
 #endif
 constexpr int kHeavy = 255;    // degrees clipped here by the counting pass
 

@@ -69,18 +69,21 @@ struct CountLaunch {
     size_t smem = 0;
     bool pv = false;
     bool merge = false;   // the instance with the search path for short pivot rows
+    bool win = false;     // the instance that counts one tile (a window of rows)
 };
 // Sets the kernel's shared-memory attribute and sizes the persistent grid
 // (not a stream operation: call it outside stream capture).
-CountLaunch prepare_count(const UnitLists& L, const tc_tuning& t, bool pv);
+CountLaunch prepare_count(const UnitLists& L, const tc_tuning& t, bool pv, bool win = false);
 // tlow (per-vertex counts of one graph only): zeroed 32-bit counters that
 // receive each task's share, or null to add it to the 64-bit accumulator.
 void launch_count_raw(const CountLaunch& c, const GraphView* views_dev, const UnitLists& L,
                       const tc_tuning& t, unsigned long long* ctr, cudaStream_t st,
                       unsigned* tlow = nullptr);
 // Launches the count kernel; ctr holds the queue heads and work counters.
+// win: the tile instance, reading the row window (i0, i1, tail_shift) of the view
 void launch_count(const GraphView* views_dev, const UnitLists& L, const tc_tuning& t, bool pv,
-                  unsigned long long* ctr, cudaStream_t st, bool profile, unsigned* tlow = nullptr);
+                  unsigned long long* ctr, cudaStream_t st, bool profile, unsigned* tlow = nullptr,
+                  bool win = false);
 void build_units(tc_graph* g, const tc_tuning& t, cudaStream_t st);
 void count(const tc_graph* g, const tc_tuning& t, uint64_t* total_dev, uint64_t* per_vertex_dev,
            cudaStream_t st);

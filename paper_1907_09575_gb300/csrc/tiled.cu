@@ -14,11 +14,14 @@
 // Eq. 5 as a double-buffered transfer.
 //
 // The graph's arrays live in page-locked host memory (tc_graph_offload).
-// Per tile, the tasks of J with i in I are compacted (order kept, so they
-// stay grouped by pivot) with their tails rebased onto the row buffer,
-// work units are built for the tile and the ordinary count kernel runs on
-// a view whose pivot labels start at J's first pivot.  Totals and
-// per-vertex counts accumulate over the tiles.
+// A pivot block's tasks, pivot rows and work units are built once; each
+// tile then runs the count kernel's tile instance over them with a window
+// of rows [i0, i1): tasks of other rows are skipped, tails are read from the
+// row buffer, pivot labels start at the block's first pivot.  Totals and
+// per-vertex counts accumulate over the tiles.  Row traffic is about the
+// number of pivot blocks times the rows, so tasks get the largest share of
+// the budget; row blocks are visited in alternating order so the one loaded
+// last is reused first.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -29,37 +32,8 @@
 namespace tc {
 namespace {
 
-constexpr int kT = 256;
 
-__global__ void k_tile_flags(const Task* __restrict__ tasks, int64_t count, int32_t i0, int32_t i1,
-                             int32_t* __restrict__ flags) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t i = tasks[t].i;
-        flags[t] = (i >= i0 && i < i1) ? 1 : 0;
-    }
-}
 
-// the selected tasks, in order, with their tails rebased onto the row buffer
-__global__ void k_tile_compact(const Task* __restrict__ tasks, const int32_t* __restrict__ flags,
-                               const int64_t* __restrict__ pos, int64_t count, int64_t shift,
-                               Task* __restrict__ out) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
-         t += (int64_t)gridDim.x * blockDim.x)
-        if (flags[t]) {
-            Task x = tasks[t];
-            x.start -= shift;
-            out[pos[t]] = x;
-        }
-}
-
-// tile task offsets per local pivot: the selected tasks before its first task
-__global__ void k_tile_loff(const int64_t* __restrict__ jloff, const int64_t* __restrict__ pos,
-                            int64_t npiv, int64_t* __restrict__ tloff) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j <= npiv;
-         j += (int64_t)gridDim.x * blockDim.x)
-        tloff[j] = pos[jloff[j]];
-}
 
 struct JBlock {
     int64_t j0, j1;   // pivots [j0, j1)
@@ -161,21 +135,23 @@ void host_copy_free(HostCopy* h) {
 
 void count_tiled(const tc_graph* g, int64_t budget, Alloc& al, const tc_tuning& t0, uint64_t* total_host,
                  uint64_t* per_vertex_host, TiledStats* ts, cudaStream_t st) {
-    const tc_tuning tt = clamp_tuning(t0);
+    tc_tuning tt = clamp_tuning(t0);
+    tt.merge_max_outdeg = 0;   // tiles use the table instance only
     const HostCopy* h = g->host;
     const int64_t n = g->n;
     const bool pv = per_vertex_host != nullptr && n > 0;
-    const unsigned G = (unsigned)(num_sms() * 8);
 
     // --- sizes within the budget --------------------------------------------
+    // Row traffic is about (pivot blocks) x (rows), so tasks get the largest
+    // share: every pivot block re-reads the rows below its last pivot.
     const int64_t fixed = (pv ? 8 * n : 0) + 64 * 1024;
     if (budget <= fixed) TC_FAIL(TC_ENOMEM, "tc_count_tiled: a budget of %lld bytes leaves nothing for tiles "
                                             "(%lld needed before any tile)", (long long)budget, (long long)fixed);
-    const int64_t avail = (budget - fixed) * 3 / 4;    // the rest: units, scan scratch, alignment
-    const int64_t capI = std::max<int64_t>(avail * 4 / 10 / 8, 1);   // row entries per row block
-    const int64_t capJ = std::max<int64_t>(avail / 10 / 8, 1);       // row entries of a pivot block
-    const int64_t capT = std::max<int64_t>(avail * 35 / 100 / 44, 1);  // tasks of a pivot block
-    const int64_t capP = std::max<int64_t>(avail * 5 / 100 / 48, 1);   // pivots of a pivot block
+    const int64_t avail = (budget - fixed) * 4 / 5;    // the rest: units, scan scratch, alignment
+    const int64_t capI = std::max<int64_t>(avail / 4 / 8, 1);       // row entries per row block (2 buffers)
+    const int64_t capJ = std::max<int64_t>(avail * 3 / 20 / 8, 1);  // row entries of a pivot block (2 copies)
+    const int64_t capT = std::max<int64_t>(avail * 2 / 5 / 16, 1);  // tasks of a pivot block
+    const int64_t capP = std::max<int64_t>(avail / 20 / 40, 1);     // pivots of a pivot block
     const int64_t maxrow = g->stats.max_outdeg;
     if (maxrow > capI || maxrow > capJ)
         TC_FAIL(TC_ENOMEM, "tc_count_tiled: a row of %lld entries does not fit a budget of %lld bytes",
@@ -230,39 +206,47 @@ void count_tiled(const tc_graph* g, int64_t budget, Alloc& al, const tc_tuning& 
     Buf<GraphView> view(al, 1);
     Buf<int64_t> vpre(al, 2);
     Buf<int32_t> rows[2] = {Buf<int32_t>(al, (size_t)(capI + capJ)), Buf<int32_t>(al, (size_t)(capI + capJ))};
-    Buf<Task> jtasks(al, (size_t)maxT), ttasks(al, (size_t)maxT);
-    Buf<int32_t> flags(al, (size_t)maxT);
-    Buf<int64_t> pos(al, (size_t)maxT + 1);
-    Buf<int64_t> joff(al, (size_t)maxP + 1), jloff(al, (size_t)maxP + 1), tloff(al, (size_t)maxP + 1);
+    Buf<Task> jtasks(al, (size_t)maxT);
+    Buf<int64_t> joff(al, (size_t)maxP + 1), jloff(al, (size_t)maxP + 1);
     TC_CUDA(cudaMemsetAsync(ctr.get(), 0, sizeof(unsigned long long) * CTR_COUNT, st));
     if (pv) TC_CUDA(cudaMemsetAsync(tnew.get(), 0, sizeof(uint64_t) * (size_t)n, st));
     Streams S;
     std::vector<int64_t> hj(maxP + 1), hl(maxP + 1);
-    int64_t ntile = 0;   // tiles issued (double-buffer slot = ntile % 2)
-    if (ts) *ts = TiledStats{};
+    int64_t holds[2] = {-1, -1};   // the row block each buffer holds
     if (ts) {
+        *ts = TiledStats{};
         ts->pivot_blocks = (int64_t)jb.size();
         ts->row_blocks = (int64_t)ib.size();
         ts->split_pivots = split_pivots;
     }
-
-    // the row blocks a pivot block needs: every I with i0 < j1 (tasks have i < j)
-    auto upload_rows = [&](const IBlock& b, int slot) {
-        const int64_t r0 = off_h(g, b.i0), r1 = off_h(g, b.i1);
+    // row block a into buffer slot, on the copy stream, once the count that
+    // last read that buffer is done
+    auto upload_rows = [&](int64_t a, int slot) {
+        const int64_t r0 = off_h(g, ib[a].i0), r1 = off_h(g, ib[a].i1);
         TC_CUDA(cudaStreamWaitEvent(S.copy, S.freed[slot], 0));
         if (r1 > r0)
             TC_CUDA(cudaMemcpyAsync(rows[slot].get(), h->adj + r0, 4 * (size_t)(r1 - r0),
                                     cudaMemcpyHostToDevice, S.copy));
         TC_CUDA(cudaEventRecord(S.ready[slot], S.copy));
+        holds[slot] = a;
         if (ts) ts->h2d_bytes += 4 * (r1 - r0);
     };
-    // both buffers start free
-    for (int b = 0; b < 2; ++b) TC_CUDA(cudaEventRecord(S.freed[b], st));
+    for (int b = 0; b < 2; ++b) {
+        TC_CUDA(cudaEventRecord(S.freed[b], st));
+        TC_CUDA(cudaEventRecord(S.ready[b], S.copy));
+    }
 
-    for (const JBlock& b : jb) {
+    for (size_t bi = 0; bi < jb.size(); ++bi) {
+        const JBlock& b = jb[bi];
         const int64_t nJ = b.j1 - b.j0, Tb = b.t1 - b.t0;
         const int64_t c0 = off_h(g, b.j0), c1 = off_h(g, b.j1);
-        // pivot rows into the top of both buffers, tasks, local offsets
+        // the row blocks this pivot block needs (tasks have i < j), in
+        // alternating order so the block loaded last is needed first next
+        std::vector<int64_t> need;
+        for (int64_t a = 0; a < (int64_t)ib.size(); ++a)
+            if (ib[a].i0 < b.j1) need.push_back(a);
+        if (bi % 2) std::reverse(need.begin(), need.end());
+        // pivot rows into the top of both buffers, tasks and local offsets
         for (int s = 0; s < 2; ++s) {
             TC_CUDA(cudaStreamWaitEvent(st, S.freed[s], 0));
             if (c1 > c0)
@@ -279,71 +263,61 @@ void count_tiled(const tc_graph* g, int64_t budget, Alloc& al, const tc_tuning& 
         TC_CUDA(cudaMemcpyAsync(joff.get(), hj.data(), 8 * (size_t)(nJ + 1), cudaMemcpyHostToDevice, st));
         TC_CUDA(cudaMemcpyAsync(jloff.get(), hl.data(), 8 * (size_t)(nJ + 1), cudaMemcpyHostToDevice, st));
         if (ts) ts->h2d_bytes += 4 * (c1 - c0) * 2 + (int64_t)sizeof(Task) * Tb + 16 * (nJ + 1);
-        std::vector<const IBlock*> need;
-        for (const IBlock& r : ib)
-            if (r.i0 < b.j1) need.push_back(&r);
-        // the first row block of this pivot block goes out now; each tile
-        // then sends the next one before it counts
-        if (!need.empty()) upload_rows(*need[0], (int)(ntile % 2));
-        for (size_t a = 0; a < need.size(); ++a) {
-            const int slot = (int)((ntile + a) % 2);
-            if (a + 1 < need.size()) upload_rows(*need[a + 1], (int)((ntile + a + 1) % 2));
-            const IBlock& r = *need[a];
-            {
-                Prof prof_("k_tile_flags", st);
-                k_tile_flags<<<grid_for(Tb, kT, G), kT, 0, st>>>(jtasks.get(), Tb, (int32_t)r.i0,
-                                                                   (int32_t)r.i1, flags.get());
+        // work units of the whole pivot block, built once; each tile runs
+        // them with its row window and skips tasks of other rows
+        GraphView v{};
+        v.off = joff.get();
+        v.off64 = 1;
+        v.adj = rows[0].get();
+        v.loff = jloff.get();
+        v.tasks = jtasks.get();
+        v.tnew = pv ? reinterpret_cast<unsigned long long*>(tnew.get()) : nullptr;
+        v.total = ctr.get() + CTR_TOTAL;
+        v.n = nJ;
+        v.jbase = (int32_t)b.j0;
+        v.i0 = 0;
+        v.i1 = 0;
+        const int64_t hv[2] = {0, nJ};
+        TC_CUDA(cudaMemcpyAsync(view.get(), &v, sizeof(v), cudaMemcpyHostToDevice, st));
+        TC_CUDA(cudaMemcpyAsync(vpre.get(), hv, sizeof(hv), cudaMemcpyHostToDevice, st));
+        UnitPlan P;
+        plan_units(P, view.get(), vpre.get(), 1, nJ, tt, al, st);
+        int64_t cnt[2] = {0, 0};
+        TC_CUDA(cudaMemcpyAsync(&cnt[0], P.ps.get() + nJ, 8, cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaMemcpyAsync(&cnt[1], P.pl.get() + nJ, 8, cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaStreamSynchronize(st));
+        UnitLists L = fill_units(P, cnt[0], cnt[1], al, st);
+        try {
+            for (size_t a = 0; a < need.size(); ++a) {
+                const int64_t blk = need[a];
+                int slot = holds[0] == blk ? 0 : holds[1] == blk ? 1 : -1;
+                if (slot < 0) {
+                    // the buffer not holding the row block counted just before
+                    slot = (a > 0 && holds[0] == need[a - 1]) ? 1 : 0;
+                    upload_rows(blk, slot);
+                }
+                // the next row block goes out while this tile counts
+                if (a + 1 < need.size()) {
+                    const int64_t nb = need[a + 1];
+                    if (holds[0] != nb && holds[1] != nb) upload_rows(nb, 1 - slot);
+                }
+                v.adj = rows[slot].get();
+                v.i0 = (int32_t)ib[blk].i0;
+                v.i1 = (int32_t)ib[blk].i1;
+                v.tail_shift = off_h(g, ib[blk].i0);
+                TC_CUDA(cudaMemcpyAsync(view.get(), &v, sizeof(v), cudaMemcpyHostToDevice, st));
+                TC_CUDA(cudaStreamWaitEvent(st, S.ready[slot], 0));
+                TC_CUDA(cudaMemsetAsync(ctr.get() + CTR_SMALL_HEAD, 0, 2 * sizeof(unsigned long long), st));
+                launch_count(view.get(), L, tt, pv, ctr.get(), st, true, nullptr, true);
+                TC_CUDA(cudaEventRecord(S.freed[slot], st));
+                if (ts) ts->tiles += 1;
             }
-            TC_LAUNCH_CHECK();
-            exclusive_scan_i32_to_i64(flags.get(), pos.get(), Tb, pos.get() + Tb, al, st);
-            {
-                Prof prof_("k_tile_compact", st);
-                k_tile_compact<<<grid_for(Tb, kT, G), kT, 0, st>>>(jtasks.get(), flags.get(), pos.get(), Tb,
-                                                                     off_h(g, r.i0), ttasks.get());
-            }
-            TC_LAUNCH_CHECK();
-            {
-                Prof prof_("k_tile_loff", st);
-                k_tile_loff<<<grid_for(nJ + 1, kT, G), kT, 0, st>>>(jloff.get(), pos.get(), nJ, tloff.get());
-            }
-            TC_LAUNCH_CHECK();
-            GraphView v{};
-            v.off = joff.get();
-            v.off64 = 1;
-            v.adj = rows[slot].get();
-            v.loff = tloff.get();
-            v.tasks = ttasks.get();
-            v.tnew = pv ? reinterpret_cast<unsigned long long*>(tnew.get()) : nullptr;
-            v.total = ctr.get() + CTR_TOTAL;
-            v.n = nJ;
-            v.jbase = (int32_t)b.j0;
-            const int64_t hv[2] = {0, nJ};
-            TC_CUDA(cudaMemcpyAsync(view.get(), &v, sizeof(v), cudaMemcpyHostToDevice, st));
-            TC_CUDA(cudaMemcpyAsync(vpre.get(), hv, sizeof(hv), cudaMemcpyHostToDevice, st));
-            UnitPlan P;
-            plan_units(P, view.get(), vpre.get(), 1, nJ, tt, al, st);
-            int64_t cnt[3] = {0, 0, 0};
-            TC_CUDA(cudaMemcpyAsync(&cnt[0], P.ps.get() + nJ, 8, cudaMemcpyDeviceToHost, st));
-            TC_CUDA(cudaMemcpyAsync(&cnt[1], P.pl.get() + nJ, 8, cudaMemcpyDeviceToHost, st));
-            TC_CUDA(cudaMemcpyAsync(&cnt[2], pos.get() + Tb, 8, cudaMemcpyDeviceToHost, st));
-            TC_CUDA(cudaStreamSynchronize(st));
-            UnitLists L = fill_units(P, cnt[0], cnt[1], al, st);
-            TC_CUDA(cudaStreamWaitEvent(st, S.ready[slot], 0));
-            TC_CUDA(cudaMemsetAsync(ctr.get() + CTR_SMALL_HEAD, 0, 2 * sizeof(unsigned long long), st));
-            try {
-                launch_count(view.get(), L, tt, pv, ctr.get(), st, true, nullptr);
-            } catch (...) {
-                al.put(L.mem, L.bytes);
-                throw;
-            }
+        } catch (...) {
             al.put(L.mem, L.bytes);
-            TC_CUDA(cudaEventRecord(S.freed[slot], st));
-            if (ts) {
-                ts->tiles += 1;
-                ts->tile_tasks += cnt[2];
-            }
+            throw;
         }
-        ntile += (int64_t)need.size();
+        al.put(L.mem, L.bytes);
+        if (ts) ts->tile_tasks += Tb;
     }
 
     // totals and per-vertex counts back to the host
