@@ -287,6 +287,7 @@ void count_tiled(const tc_graph* g, int64_t budget, Alloc& al, const tc_tuning& 
         TC_CUDA(cudaMemcpyAsync(&cnt[1], P.pl.get() + nJ, 8, cudaMemcpyDeviceToHost, st));
         TC_CUDA(cudaStreamSynchronize(st));
         UnitLists L = fill_units(P, cnt[0], cnt[1], al, st);
+        const CountLaunch launch = prepare_count(L, tt, pv, true);
         try {
             for (size_t a = 0; a < need.size(); ++a) {
                 const int64_t blk = need[a];
@@ -308,7 +309,10 @@ void count_tiled(const tc_graph* g, int64_t budget, Alloc& al, const tc_tuning& 
                 TC_CUDA(cudaMemcpyAsync(view.get(), &v, sizeof(v), cudaMemcpyHostToDevice, st));
                 TC_CUDA(cudaStreamWaitEvent(st, S.ready[slot], 0));
                 TC_CUDA(cudaMemsetAsync(ctr.get() + CTR_SMALL_HEAD, 0, 2 * sizeof(unsigned long long), st));
-                launch_count(view.get(), L, tt, pv, ctr.get(), st, true, nullptr, true);
+                if (L.nlarge + L.nsmall > 0) {
+                    Prof prof_("k_count", st);
+                    launch_count_raw(launch, view.get(), L, tt, ctr.get(), st, nullptr);
+                }
                 TC_CUDA(cudaEventRecord(S.freed[slot], st));
                 if (ts) ts->tiles += 1;
             }

@@ -90,7 +90,7 @@ def test_heavy_pivot_split_over_pivot_blocks(tc):
     g, hs, hd, st, arena = offloaded(tc, spec)
     want, want_t = oracle.count(hs, hd, spec.n, per_vertex=True)
     assert st["max_deg"] > 8000
-    budget = 8 * spec.n + (1 << 20)
+    budget = 8 * spec.n + (64 << 10) + (450 << 10)   # a pivot block holds ~9K tasks
     cap = CappedAllocator(tc, budget)
     total, t, ts = g.count_tiled(budget, per_vertex=True, allocator=cap.struct)
     assert total == want and np.array_equal(t, want_t)
