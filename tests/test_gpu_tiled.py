@@ -84,18 +84,30 @@ def test_rmat_scale20_within_an_eighth_of_its_arena(tc):
 
 
 def test_heavy_pivot_split_over_pivot_blocks(tc):
-    """A skewed graph whose hubs have more tasks than a pivot block holds: a
-    pivot's tasks are spread over several blocks."""
-    spec = inputs.chung_lu_graph(3, n=100_000, mean_degree=24.0, wmax=2e4)
-    g, hs, hd, st, arena = offloaded(tc, spec)
-    want, want_t = oracle.count(hs, hd, spec.n, per_vertex=True)
-    assert st["max_deg"] > 8000
-    budget = 8 * spec.n + (64 << 10) + (450 << 10)   # a pivot block holds ~9K tasks
+    """A pivot with more tasks than a pivot block holds: vertex 0 is joined
+    to 20,000 leaves and every leaf also to vertex 1 (above 0 in the order),
+    so pivot 0 has a task per leaf, each hitting vertex 1; RMAT edges among
+    the leaves add structure.  Its tasks are spread over several blocks."""
+    leaves = 20000
+    n = leaves + 2
+    rs, rd = inputs.rmat(7, 14, 200000)
+    hs = np.concatenate([np.zeros(leaves, np.int32), np.ones(leaves, np.int32), [0],
+                         (rs % leaves + 2).astype(np.int32)]).astype(np.int32)
+    hd = np.concatenate([np.arange(2, n, dtype=np.int32), np.arange(2, n, dtype=np.int32), [1],
+                         (rd % leaves + 2).astype(np.int32)]).astype(np.int32)
+    want, want_t = oracle.count(hs, hd, n, per_vertex=True)
+    g = tc.preprocess(torch.from_numpy(hs).cuda(), torch.from_numpy(hd).cuda(), n, offsets=64)
+    st = g.stats()
+    g.count()
+    count_probes = sum(g.count_stats()["probes"])
+    g.offload()
+    budget = 8 * n + (64 << 10) + (600 << 10)       # a pivot block holds ~12K tasks
     cap = CappedAllocator(tc, budget)
     total, t, ts = g.count_tiled(budget, per_vertex=True, allocator=cap.struct)
     assert total == want and np.array_equal(t, want_t)
     assert cap.refused == 0 and cap.peak <= budget
     assert ts["split_pivots"] >= 1 and ts["tile_tasks"] == st["tasks"]
+    assert ts["probes"] == count_probes
     g.free()
 
 
