@@ -137,14 +137,6 @@ void exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t count,
 // TC_ETIMEOUT itself.
 void radix_sort_u64(uint64_t** keys, uint64_t** alt, int64_t count, int lo, int hi,
                     Alloc& al, cudaStream_t st, int* err_dev = nullptr);
-// The same sort of the canonical keys of undirected pairs, made on the fly by
-// the digit count and the first pass (min << bits | max; self-loops and ids
-// outside [0, n) become `sentinel`, the latter also setting bit 1 of
-// *err_dev): no key array is written first.  Sorted keys end up in *keys
-// (both buffers hold count keys).
-void radix_sort_pairs(const int32_t* src, const int32_t* dst, int64_t count, int64_t n, int bits,
-                      uint64_t sentinel, uint64_t** keys, uint64_t** alt, Alloc& al, cudaStream_t st,
-                      int* err_dev);
 // One warp waits, with the radix look-back's bounded wait, on a word nothing
 // publishes; true when the bound ran out and was reported (synchronises).
 bool selftest_wait_timeout(long limit, Alloc& al, cudaStream_t st);

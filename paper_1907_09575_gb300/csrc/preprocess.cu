@@ -4,11 +4,9 @@
 //   a2 unique         up to 2^26 pairs: keys inserted into a device hash set
 //                     (open addressing, load <= 1/2) whose compacted slots
 //                     are E, in no particular order (a5 sorts them).  Larger
-//                     inputs: LSD radix sort whose digit count and first pass
-//                     make the canonical keys from the pairs, first of each
-//                     run kept -- the set's random atomics into a table of
-//                     2^31 slots ran slower than the sort's passes (measured
-//                     at 2^30 pairs).
+//                     inputs: LSD radix sort, first of each run kept -- the
+//                     set's random atomics into a table of 2^31 slots ran
+//                     slower than the sort's passes (measured at 2^30 pairs).
 //   a3 degrees        d(v) counted when a key enters the set / from the
 //                     unique runs
 //   a4 relabel        rank by (d(v), v): the counting sort of Section 5.3 as
@@ -138,6 +136,23 @@ __device__ __forceinline__ void warp_add_sorted(int32_t* counter, int32_t v, boo
         // run length: 1 + the continuation lanes right after this one
         const unsigned rest = lane == 31 ? 0u : (C >> (lane + 1));
         atomicAdd(&counter[v], 1 + __ffs(~rest) - 1);
+    }
+}
+
+__global__ void k_canon(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                        int64_t P, int64_t n, int bits, uint64_t sentinel,
+                        uint64_t* __restrict__ keys, int* __restrict__ err) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int32_t a = src[e], b = dst[e];
+        uint64_t k = sentinel;
+        if (a < 0 || b < 0 || (int64_t)a >= n || (int64_t)b >= n) {
+            atomicOr(err, 1);
+        } else if (a != b) {
+            uint64_t lo = (uint64_t)min(a, b), hi = (uint64_t)max(a, b);
+            k = (lo << bits) | hi;
+        }
+        keys[e] = k;
     }
 }
 
@@ -564,21 +579,27 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
         }
         TC_LAUNCH_CHECK();
     } else if (P > 0) {
-        // canonical keys, radix sorted, first of each run kept: the digit
-        // count and the first pass make each key from its pair (no key array
-        // is written first)
+        // canonical keys, radix sorted, first of each run kept (making the
+        // keys inside the sort's digit count and first pass, from the two
+        // pair arrays, was slower: 19 ms against 14 for this pass, a key
+        // pass and its share of the digit count)
         const uint64_t sentinel = (bits * 2 >= 64) ? ~0ull : ((1ull << (2 * bits)) - 1ull);
         ab = Buf<uint64_t>(al, (size_t)P);
         alt = ab.get();
+        {
+            Prof prof_("k_canon", st);
+            k_canon<<<grid_for(P, kT, G), kT, 0, st>>>(src, dst, P, n, bits, sentinel, keys, scal.get());
+        }
+        TC_LAUNCH_CHECK();
         if (num_comps > 0) {
             Prof prof_("k_check_comp", st);
             k_check_comp<<<grid_for(P, kT, G), kT, 0, st>>>(src, dst, P, vpre.get(), num_comps, scal.get());
         }
         TC_LAUNCH_CHECK();
-        // ids outside [0, n) became sentinels; the error is read at the next sync
-        radix_sort_pairs(src, dst, P, n, bits, sentinel, &keys, &alt, al, st, scal.get());
         hsrc.release();
         hdst.release();
+        // ids outside [0, n) became sentinels; the error is read at the next sync
+        radix_sort_u64(&keys, &alt, P, 0, 2 * bits, al, st, scal.get());
         {
             Buf<int32_t> fl(al, (size_t)P);
             Buf<int64_t> pos(al, (size_t)P);

@@ -25,31 +25,6 @@ constexpr int kSeg = kTile / kWarps;       // 512 keys per warp segment
 constexpr int kRounds = kSeg / 32;         // 16 rounds of 32 keys
 constexpr int kRadix = 256;
 
-// Where a pass reads its keys: a key array, or the canonical keys of
-// undirected pairs made on the fly (min << bits | max; self-loops and ids
-// outside [0, n) become the sentinel, which sorts last).
-struct KeysIn {
-    const uint64_t* k;
-    __device__ __forceinline__ uint64_t operator()(int64_t i) const { return k[i]; }
-    __device__ __forceinline__ bool bad(int64_t) const { return false; }
-};
-struct PairsIn {
-    const int32_t* src;
-    const int32_t* dst;
-    int64_t n;
-    int bits;
-    uint64_t sentinel;
-    __device__ __forceinline__ bool bad(int64_t i) const {
-        const int32_t a = src[i], b = dst[i];
-        return a < 0 || b < 0 || (int64_t)a >= n || (int64_t)b >= n;
-    }
-    __device__ __forceinline__ uint64_t operator()(int64_t i) const {
-        const int32_t a = src[i], b = dst[i];
-        if (a < 0 || b < 0 || (int64_t)a >= n || (int64_t)b >= n || a == b) return sentinel;
-        return ((uint64_t)min(a, b) << bits) | (uint64_t)max(a, b);
-    }
-};
-
 __device__ __forceinline__ unsigned digit_of(uint64_t k, int shift, unsigned mask) {
     return (unsigned)(k >> shift) & mask;
 }
@@ -106,18 +81,16 @@ __global__ void k_wait_selftest(const unsigned long long* word, long limit, int*
 }
 
 // Global digit counts of every pass: hist[pass][digit], bits [lo, hi).
-// With pairs as input, an id outside [0, n) also sets bit 1 of *err.
-template <class In>
-__global__ void __launch_bounds__(kThreads) k_digit_hist(In keys, int64_t count, int lo, int npass, int hi,
-                                                         unsigned long long* __restrict__ hist, int* err) {
+__global__ void __launch_bounds__(kThreads) k_digit_hist(const uint64_t* __restrict__ keys,
+                                                         int64_t count, int lo, int npass, int hi,
+                                                         unsigned long long* __restrict__ hist) {
     __shared__ unsigned h[kMaxPasses][kRadix];
     for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += kThreads) (&h[0][0])[i] = 0;
     __syncthreads();
     for (int64_t base = blockIdx.x * (int64_t)kThreads; base < count; base += (int64_t)gridDim.x * kThreads) {
         const int64_t idx = base + threadIdx.x;
         const bool valid = idx < count;
-        const uint64_t k = valid ? keys(idx) : 0;
-        if (valid && keys.bad(idx)) atomicOr(err, 1);
+        const uint64_t k = valid ? keys[idx] : 0;
         for (int p = 0; p < npass; ++p) {
             const int shift = lo + 8 * p;
             const unsigned mask = (1u << min(8, hi - shift)) - 1u;
@@ -160,8 +133,8 @@ __global__ void __launch_bounds__(kRadix) k_digit_offsets(unsigned long long* __
     h[d] = before + inc - c;
 }
 
-template <class In>
-__global__ void __launch_bounds__(kThreads, 4) k_onesweep(In in, uint64_t* __restrict__ out, int64_t count,
+__global__ void __launch_bounds__(kThreads, 4) k_onesweep(const uint64_t* __restrict__ in,
+                                                          uint64_t* __restrict__ out, int64_t count,
                                                           int shift, int nbits,
                                                           const unsigned long long* __restrict__ goff,
                                                           unsigned long long* status,
@@ -185,7 +158,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(In in, uint64_t* __res
 #pragma unroll
     for (int k = 0; k < kItems; ++k) {
         const int p = k * kThreads + threadIdx.x;
-        if (p < valid_in_tile) stage[p] = in(tbase + p);
+        if (p < valid_in_tile) stage[p] = in[tbase + p];
     }
     __syncthreads();
     const int seg = w * kSeg;
@@ -281,13 +254,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_onesweep(In in, uint64_t* __res
 
 }  // namespace
 
-namespace {
-
-// The sort proper: the first pass reads `first` (keys or pairs), every later
-// pass the keys the previous one wrote.
-template <class In>
-void radix_sort_from(In first, uint64_t** keys, uint64_t** alt, int64_t count, int lo, int hi, Alloc& al,
-                     cudaStream_t st, int* err_dev) {
+void radix_sort_u64(uint64_t** keys, uint64_t** alt, int64_t count, int lo, int hi, Alloc& al,
+                    cudaStream_t st, int* err_dev) {
+    if (count <= 1 || hi <= lo) return;
     const int64_t ntiles = (count + kTile - 1) / kTile;
     const int npass = (hi - lo + 7) / 8;
     // [hist: kMaxPasses x 256 u64][tile counters: kMaxPasses u32][error flag]
@@ -299,7 +268,7 @@ void radix_sort_from(In first, uint64_t** keys, uint64_t** alt, int64_t count, i
     {
         Prof prof_("k_digit_hist", st);
         k_digit_hist<<<grid_for(count, kThreads, (int64_t)num_sms() * 8), kThreads, 0, st>>>(
-            first, count, lo, npass, hi, hist.get(), err);
+            *keys, count, lo, npass, hi, hist.get());
     }
     TC_LAUNCH_CHECK();
     {
@@ -313,13 +282,9 @@ void radix_sort_from(In first, uint64_t** keys, uint64_t** alt, int64_t count, i
         TC_CUDA(cudaMemsetAsync(status.get(), 0, sizeof(unsigned long long) * (size_t)ntiles * kRadix, st));
         {
             Prof prof_("k_onesweep", st);
-            if (p == 0)
-                k_onesweep<<<(unsigned)ntiles, kThreads, 0, st>>>(first, *alt, count, shift, nbits,
-                                                                  hist.get(), status.get(), ctrs, err);
-            else
-                k_onesweep<<<(unsigned)ntiles, kThreads, 0, st>>>(KeysIn{*keys}, *alt, count, shift, nbits,
-                                                                  hist.get() + (size_t)p * kRadix,
-                                                                  status.get(), ctrs + p, err);
+            k_onesweep<<<(unsigned)ntiles, kThreads, 0, st>>>(*keys, *alt, count, shift, nbits,
+                                                              hist.get() + (size_t)p * kRadix,
+                                                              status.get(), ctrs + p, err);
         }
         TC_LAUNCH_CHECK();
         uint64_t* t = *keys;
@@ -330,27 +295,7 @@ void radix_sort_from(In first, uint64_t** keys, uint64_t** alt, int64_t count, i
     int herr = 0;
     TC_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     TC_CUDA(cudaStreamSynchronize(st));
-    if (herr & 4) TC_FAIL(TC_ETIMEOUT, "radix sort: a look-back wait ran past its bound");
-}
-
-}  // namespace
-
-void radix_sort_u64(uint64_t** keys, uint64_t** alt, int64_t count, int lo, int hi, Alloc& al,
-                    cudaStream_t st, int* err_dev) {
-    if (count <= 1 || hi <= lo) return;
-    radix_sort_from(KeysIn{*keys}, keys, alt, count, lo, hi, al, st, err_dev);
-}
-
-void radix_sort_pairs(const int32_t* src, const int32_t* dst, int64_t count, int64_t n, int bits,
-                      uint64_t sentinel, uint64_t** keys, uint64_t** alt, Alloc& al, cudaStream_t st,
-                      int* err_dev) {
-    const PairsIn in{src, dst, n, bits, sentinel};
-    if (count == 0) return;
-    if (count == 1) {   // nothing to order: the one canonical key, checked
-        radix_sort_from(in, keys, alt, 1, 0, 8, al, st, err_dev);
-        return;
-    }
-    radix_sort_from(in, keys, alt, count, 0, 2 * bits, al, st, err_dev);
+    if (herr) TC_FAIL(TC_ETIMEOUT, "radix sort: a look-back wait ran past its bound");
 }
 
 }  // namespace tc
