@@ -44,12 +44,6 @@ constexpr int kEmpty = -1;
 #define TC_UNROLL 4
 #endif
 constexpr int kUnroll = TC_UNROLL;   // independent loads in flight per lane
-#ifndef TC_LPT
-#define TC_LPT 0               // long tails of at least this many entries are walked first (0: off)
-#endif
-#ifndef TC_RANK2
-#define TC_RANK2 0             // per-vertex rank as prefix + popc of the bits up to the hit
-#endif
 #ifndef TC_PV_BRANCHLESS
 #define TC_PV_BRANCHLESS 1     // per-vertex bitmap probe: 1 computes the rank on every lane
 #endif
@@ -147,14 +141,9 @@ struct BitTab {
         const unsigned b = d & 31;
         const unsigned h = (w >> b) & 1u;
         mine += h;
-#if TC_RANK2
         // popc of the bits up to and including b counts the hit itself
         const int r1 = (int)pre[d >> 5] + __popc(w << (b ^ 31u));
         if (h) atomicAdd(&cnt[r1 - 1], 1u);
-#else
-        const int r = (int)pre[d >> 5] + __popc(w & ((1u << b) - 1u));
-        if (h) atomicAdd(&cnt[r], 1u);
-#endif
     }
     // hit counters by rank (rank < slice <= 4096): one word each, so hits on
     // neighbouring entries never share an atomic's word
@@ -371,32 +360,12 @@ __device__ __forceinline__ void warp_probe_group(const Task* __restrict__ tasks,
     const bool lg = valid && len >= 32;
     unsigned longm = __ballot_sync(0xffffffffu, lg);
     if (defer) {
-#if TC_LPT
-        // the longest tails from the front of the queue, the rest from the
-        // back (ndefer[2] counts those), so the longest are walked first
-        const unsigned vlm = __ballot_sync(0xffffffffu, lg && len >= TC_LPT);
-        const unsigned rest = longm & ~vlm;
-        if (vlm) {
-            int slot = 0;
-            if (lane == 0) slot = atomicAdd(ndefer, __popc(vlm));
-            slot = __shfl_sync(0xffffffffu, slot, 0);
-            if ((vlm >> lane) & 1u) defer[slot + __popc(vlm & (le >> 1))] = (unsigned short)(t - t0);
-        }
-        if (rest) {
-            int slot = 0;
-            if (lane == 0) slot = atomicAdd(ndefer + 2, __popc(rest));
-            slot = __shfl_sync(0xffffffffu, slot, 0);
-            if ((rest >> lane) & 1u)
-                defer[(int)(t1 - t0) - 1 - (slot + __popc(rest & (le >> 1)))] = (unsigned short)(t - t0);
-        }
-#else
         if (longm) {
             int slot = 0;
             if (lane == 0) slot = atomicAdd(ndefer, __popc(longm));
             slot = __shfl_sync(0xffffffffu, slot, 0);
             if (lg) defer[slot + __popc(longm & (le >> 1))] = (unsigned short)(t - t0);
         }
-#endif
     } else {
         while (longm) {
             const int o = __ffs(longm) - 1;
@@ -621,16 +590,7 @@ __device__ __forceinline__ void cta_probe_unit(const GraphView& G, const Unit& U
                                   &s_ctl[1], uh, probes, TaskWindow{G.i0, G.i1, G.tail_shift});
     }
     __syncthreads();
-#if TC_LPT
-    const int nfront = s_ctl[1];
-    const int nlong = nfront + s_ctl[3];
-    const int qcap = (int)(U.t1 - U.t0);
-    // queue position x: the front part in order, then the back part
-    auto qidx = [&](int x) { return x < nfront ? x : qcap - 1 - (x - nfront); };
-#else
     const int nlong = s_ctl[1];
-    auto qidx = [](int x) { return x; };
-#endif
     auto pop = [&]() {
         int v = 0;
         if (lane == 0) v = atomicAdd(&s_ctl[2], 1);
@@ -642,7 +602,7 @@ __device__ __forceinline__ void cta_probe_unit(const GraphView& G, const Unit& U
         Task t;
         t.len = 0;
         if (x < nlong) {
-            t = tasks[U.t0 + s_long[qidx(x)]];
+            t = tasks[U.t0 + s_long[x]];
             t.start -= shift;
         }
         return t;
@@ -674,7 +634,7 @@ __device__ __forceinline__ void cta_probe_unit(const GraphView& G, const Unit& U
         Task cur;
         cur.len = 0;
         if (x < nlong) {
-            cur = tasks[U.t0 + s_long[qidx(x)]];
+            cur = tasks[U.t0 + s_long[x]];
             cur.start -= shift;
         }
         while (x < nlong) {
@@ -682,7 +642,7 @@ __device__ __forceinline__ void cta_probe_unit(const GraphView& G, const Unit& U
             Task nxt;
             nxt.len = 0;
             if (xn < nlong) {
-                nxt = tasks[U.t0 + s_long[qidx(xn)]];
+                nxt = tasks[U.t0 + s_long[xn]];
                 nxt.start -= shift;
                 if (32 * lane < nxt.len)
                     asm volatile("prefetch.global.L2 [%0];" ::"l"(adj + nxt.start + 32 * lane));
@@ -816,7 +776,6 @@ __global__ void __launch_bounds__(256, TC_LARGE_MINB)
             s_ctl[0] = 0;
             s_ctl[1] = 0;
             s_ctl[2] = 0;
-            s_ctl[3] = 0;
         }
         __syncthreads();
         const long long u = s_unit;
