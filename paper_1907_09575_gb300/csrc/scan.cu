@@ -94,6 +94,38 @@ __global__ void __launch_bounds__(kThreads) k_tile_scan(const Tin* in, int64_t* 
         *total = run;  // the last thread's running sum after its items = grand total
 }
 
+// Arrays of up to kBlockMax entries in one launch: one block, each thread a
+// contiguous chunk (summed, scanned across the block, then written).
+constexpr int kBlockThreads = 1024;
+constexpr int64_t kBlockMax = 64ll * kBlockThreads;
+
+template <class Tin>
+__global__ void __launch_bounds__(kBlockThreads) k_block_scan(const Tin* in, int64_t* out, int64_t count,
+                                                              int64_t* total) {
+    __shared__ int64_t warp_sums[kBlockThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t per = (count + kBlockThreads - 1) / kBlockThreads;
+    const int64_t b = min64((int64_t)threadIdx.x * per, count), e = min64(b + per, count);
+    int64_t s = 0;
+    for (int64_t i = b; i < e; ++i) s += (int64_t)in[i];
+    int64_t inc = warp_incl_scan(s);
+    if (lane == 31) warp_sums[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int64_t x = warp_sums[lane];
+        x = warp_incl_scan(x);
+        warp_sums[lane] = x;
+    }
+    __syncthreads();
+    int64_t run = (w > 0 ? warp_sums[w - 1] : 0) + inc - s;
+    for (int64_t i = b; i < e; ++i) {
+        const int64_t v = (int64_t)in[i];   // in may alias out: read before the write
+        out[i] = run;
+        run += v;
+    }
+    if (total && threadIdx.x == kBlockThreads - 1) *total = warp_sums[kBlockThreads / 32 - 1];
+}
+
 template <class Tin>
 void scan_impl(const Tin* in, int64_t* out, int64_t count, int64_t* total_dev, Alloc& al,
                cudaStream_t st) {
@@ -102,6 +134,14 @@ void scan_impl(const Tin* in, int64_t* out, int64_t count, int64_t* total_dev, A
         return;
     }
     int64_t tiles = (count + kTile - 1) / kTile;
+    if (tiles > 1 && count <= kBlockMax) {
+        {
+            Prof prof_("k_block_scan", st);
+            k_block_scan<Tin><<<1, kBlockThreads, 0, st>>>(in, out, count, total_dev);
+        }
+        TC_LAUNCH_CHECK();
+        return;
+    }
     if (tiles == 1) {
         {
             Prof prof_("k_tile_scan", st);
