@@ -117,15 +117,20 @@ bool tuning_equal(const tc_tuning& a, const tc_tuning& b) {
     return std::memcmp(&a, &b, sizeof(tc_tuning)) == 0;
 }
 
-// Five timing events, destroyed with the scope.
+// Five timing events per host thread and device, created at the thread's
+// first call on that device and kept (never destroyed: they live as long as
+// the process).
 struct Events {
     cudaEvent_t e[5] = {};
     Events() {
-        for (auto& x : e) TC_CUDA(cudaEventCreate(&x));
-    }
-    ~Events() {
-        for (auto& x : e)
-            if (x) cudaEventDestroy(x);
+        int dev = 0;
+        TC_CUDA(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= kMaxDevices) TC_FAIL(TC_EINVAL, "device %d out of range", dev);
+        static thread_local cudaEvent_t cache[kMaxDevices][5] = {};
+        for (int k = 0; k < 5; ++k) {
+            if (!cache[dev][k]) TC_CUDA(cudaEventCreate(&cache[dev][k]));
+            e[k] = cache[dev][k];
+        }
     }
     double ms(int a, int b) const {
         float v = 0.f;

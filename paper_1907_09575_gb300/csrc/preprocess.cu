@@ -32,6 +32,9 @@ constexpr int kT = 256;
 #ifndef TC_DEGREE_COUNTING
 #define TC_DEGREE_COUNTING 1   // a4: 1 counting pass + heavy tail (Section 5.3); 0 radix on the degree bits
 #endif
+// below this many vertices the radix form takes fewer launches (the heavy
+// tail's own sort costs more than the passes it saves)
+constexpr int64_t kCountingMinVertices = 1ll << 20;
 constexpr int kHeavy = 255;    // degrees clipped here by the counting pass
 
 constexpr uint64_t kEmptyKey = ~0ull;   // no key: keys use 2b <= 62 bits
@@ -681,7 +684,7 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
         Buf<uint64_t> dk(al, (size_t)n), da(al, (size_t)n);
         uint64_t* dkeys = dk.get();
         uint64_t* dalt = da.get();
-        if (TC_DEGREE_COUNTING) {
+        if (TC_DEGREE_COUNTING && n >= kCountingMinVertices) {
             // the counting sort of Section 5.3 for degrees below kHeavy (one
             // stable pass), the heavy tail sorted on its full degrees
             {
