@@ -73,11 +73,13 @@ typedef struct {
 #define TC_OFFSETS_64      0x4u  /* force 64-bit CSR offsets */
 /* With neither offset flag, 32-bit offsets are used when m < 2^31. */
 
-/* Counting knobs.  Zero in any field selects its default.  The count never
- * depends on them; only speed does. */
+/* Counting knobs.  Zero in any field selects its default (some defaults
+ * depend on the graph's size; tc_tuning_default leaves those at zero).  The
+ * count never depends on them; only speed does. */
 typedef struct {
     int32_t small_max_outdeg;  /* pivots with |U_j| <= this go to warp units (<= 64) */
-    int32_t warp_unit_tasks;   /* tasks per warp unit (<= 8192) */
+    int32_t warp_unit_tasks;   /* tasks per warp unit (<= 8192); 0: 16 for graphs of
+                                  fewer than 2^21 edges, else 64 */
     int32_t cta_unit_tasks;    /* tasks per CTA unit (<= 8192) */
     int32_t cta_threads;       /* threads per CTA of the large-pivot kernel (64..256) */
     int32_t slice_max;         /* pivot entries tabled at once by one CTA (64..4096) */

@@ -51,7 +51,9 @@ void drop_exec(tc_batch* b) {
 
 // (Re)build the unit lists for a tuning and capture the counting launch.
 void set_tuning(tc_batch* b, const tc_tuning& t) {
-    const tc_tuning tt = clamp_tuning(t);
+    int64_t m = 0;
+    for (const tc_graph* g : b->graphs) m += g->m;
+    const tc_tuning tt = clamp_tuning(size_tuning(t, m));
     drop_exec(b);
     if (b->units.mem) {
         b->alloc.put(b->units.mem, b->units.bytes);

@@ -1066,7 +1066,7 @@ void build_units(tc_graph* g, const tc_tuning& t, cudaStream_t st) {
 void count_components(const tc_graph* gc, const tc_tuning& t, uint64_t* comp_totals_dev,
                       cudaStream_t st) {
     tc_graph* g = const_cast<tc_graph*>(gc);
-    const tc_tuning tt = clamp_tuning(t);
+    const tc_tuning tt = clamp_tuning(size_tuning(t, g->m));
     if (!tuning_equal(tt, g->units_tuning)) build_units(g, tt, st);
     TC_CUDA(cudaMemsetAsync(g->counters, 0, sizeof(unsigned long long) * CTR_COUNT, st));
     TC_CUDA(cudaMemsetAsync(g->comp_totals, 0, sizeof(unsigned long long) * (size_t)g->num_comps, st));
@@ -1083,7 +1083,7 @@ void count_components(const tc_graph* gc, const tc_tuning& t, uint64_t* comp_tot
 void count(const tc_graph* gc, const tc_tuning& t, uint64_t* total_dev, uint64_t* per_vertex_dev,
            cudaStream_t st) {
     tc_graph* g = const_cast<tc_graph*>(gc);   // unit lists are a cache of the tuning
-    const tc_tuning tt = clamp_tuning(t);
+    const tc_tuning tt = clamp_tuning(size_tuning(t, g->m));
     if (!tuning_equal(tt, g->units_tuning)) build_units(g, tt, st);
     const bool pv = per_vertex_dev != nullptr;
     TC_CUDA(cudaMemsetAsync(g->counters, 0, sizeof(unsigned long long) * CTR_COUNT, st));

@@ -863,7 +863,7 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
     // as the task statistics
     tc_tuning def;
     tuning_defaults(&def);
-    def = clamp_tuning(def);
+    def = clamp_tuning(size_tuning(def, m));
     Buf<int64_t> gvpre(al, 2);
     const int64_t hv[2] = {0, n};
     TC_CUDA(cudaMemcpyAsync(gvpre.get(), hv, sizeof(hv), cudaMemcpyHostToDevice, st));

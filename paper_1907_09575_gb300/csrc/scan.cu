@@ -94,36 +94,56 @@ __global__ void __launch_bounds__(kThreads) k_tile_scan(const Tin* in, int64_t* 
         *total = run;  // the last thread's running sum after its items = grand total
 }
 
-// Arrays of up to kBlockMax entries in one launch: one block, each thread a
-// contiguous chunk (summed, scanned across the block, then written).
+// Arrays of up to kBlockMax entries in one launch: one block streams the
+// array through shared memory in chunks of kChunk entries (coalesced loads
+// and stores; each thread scans kPer contiguous entries of the chunk), the
+// running total carried from chunk to chunk.
 constexpr int kBlockThreads = 1024;
-constexpr int64_t kBlockMax = 64ll * kBlockThreads;
+constexpr int kPer = 4;
+constexpr int kChunk = kBlockThreads * kPer;
+constexpr int64_t kBlockMax = 16ll * kChunk;
 
 template <class Tin>
 __global__ void __launch_bounds__(kBlockThreads) k_block_scan(const Tin* in, int64_t* out, int64_t count,
                                                               int64_t* total) {
+    __shared__ int64_t buf[kChunk];
     __shared__ int64_t warp_sums[kBlockThreads / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t per = (count + kBlockThreads - 1) / kBlockThreads;
-    const int64_t b = min64((int64_t)threadIdx.x * per, count), e = min64(b + per, count);
-    int64_t s = 0;
-    for (int64_t i = b; i < e; ++i) s += (int64_t)in[i];
-    int64_t inc = warp_incl_scan(s);
-    if (lane == 31) warp_sums[w] = inc;
-    __syncthreads();
-    if (w == 0) {
-        int64_t x = warp_sums[lane];
-        x = warp_incl_scan(x);
-        warp_sums[lane] = x;
+    int64_t carry = 0;
+    for (int64_t c0 = 0; c0 < count; c0 += kChunk) {
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int idx = k * kBlockThreads + threadIdx.x;
+            buf[idx] = (c0 + idx < count) ? (int64_t)in[c0 + idx] : 0;
+        }
+        __syncthreads();
+        int64_t v[kPer], sum = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            v[k] = buf[threadIdx.x * kPer + k];
+            sum += v[k];
+        }
+        const int64_t inc = warp_incl_scan(sum);
+        if (lane == 31) warp_sums[w] = inc;
+        __syncthreads();
+        if (w == 0) warp_sums[lane] = warp_incl_scan(warp_sums[lane]);
+        __syncthreads();
+        int64_t run = carry + (w > 0 ? warp_sums[w - 1] : 0) + inc - sum;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            buf[threadIdx.x * kPer + k] = run;
+            run += v[k];
+        }
+        carry += warp_sums[kBlockThreads / 32 - 1];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int idx = k * kBlockThreads + threadIdx.x;
+            if (c0 + idx < count) out[c0 + idx] = buf[idx];
+        }
+        __syncthreads();   // buf and warp_sums are rewritten by the next chunk
     }
-    __syncthreads();
-    int64_t run = (w > 0 ? warp_sums[w - 1] : 0) + inc - s;
-    for (int64_t i = b; i < e; ++i) {
-        const int64_t v = (int64_t)in[i];   // in may alias out: read before the write
-        out[i] = run;
-        run += v;
-    }
-    if (total && threadIdx.x == kBlockThreads - 1) *total = warp_sums[kBlockThreads / 32 - 1];
+    if (total && threadIdx.x == 0) *total = carry;
 }
 
 template <class Tin>

@@ -23,6 +23,8 @@ void generate_rmat_multi(const RmatJob* jobs_dev, const int64_t* ppre_dev, int n
                          int32_t* src, int32_t* dst, cudaStream_t st);
 
 void tuning_defaults(tc_tuning* t);
+// Fills the knobs left to the graph's size (m edges, or the batch's total).
+tc_tuning size_tuning(const tc_tuning& t, int64_t m);
 void tuning_resolve(const tc_tuning* in, tc_tuning* out);  // fills zeros, clamps
 bool tuning_equal(const tc_tuning& a, const tc_tuning& b);
 

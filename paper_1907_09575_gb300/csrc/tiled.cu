@@ -135,7 +135,7 @@ void host_copy_free(HostCopy* h) {
 
 void count_tiled(const tc_graph* g, int64_t budget, Alloc& al, const tc_tuning& t0, uint64_t* total_host,
                  uint64_t* per_vertex_host, TiledStats* ts, cudaStream_t st) {
-    tc_tuning tt = clamp_tuning(t0);
+    tc_tuning tt = clamp_tuning(size_tuning(t0, g->m));
     tt.merge_max_outdeg = 0;   // tiles use the table instance only
     const HostCopy* h = g->host;
     const int64_t n = g->n;
