@@ -110,6 +110,8 @@ __device__ __forceinline__ unsigned bit_range(int lo, int hi) {
 // (buckets - 1) (the paper's AND hash), overflow to the next bucket; the
 // occupied slots of a bucket are a prefix, so an empty last slot ends a miss.
 // Both return a counter index for per-vertex credit (rank or slot), or -1.
+// A probe of -1 (a lane past the end of a tail) is a miss in every table:
+// the bitmap clamps it onto the guard bit, the others fail the window test.
 // ---------------------------------------------------------------------------
 struct BitTab {
     const unsigned* bm;
@@ -270,8 +272,7 @@ __device__ __forceinline__ unsigned warp_walk_tail(int64_t st, int L, const int3
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) kn[u] = (q1 + 32 * u + lane < L) ? __ldg(p + q1 + 32 * u) : -1;
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u)
-                if (k[u] >= 0) probe_one<PV>(T, k[u], cnt, mine);
+            for (int u = 0; u < kUnroll; ++u) probe_one<PV>(T, k[u], cnt, mine);   // -1: a miss
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) k[u] = kn[u];
         }
@@ -294,8 +295,7 @@ __device__ __forceinline__ unsigned warp_walk_tail(int64_t st, int L, const int3
                 k[u] = (q < L) ? __ldg(p + q0 + 32 * u) : -1;
             }
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u)
-                if (k[u] >= 0) probe_one<PV>(T, k[u], cnt, mine);
+            for (int u = 0; u < kUnroll; ++u) probe_one<PV>(T, k[u], cnt, mine);   // -1: a miss
         }
         hits += mine;
         return 0;
@@ -404,7 +404,7 @@ __device__ __forceinline__ void warp_probe_group(const Task* __restrict__ tasks,
         }
         int r[kUnroll];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) r[u] = (k[u] >= 0) ? T.template find<PV>(k[u]) : -1;
+        for (int u = 0; u < kUnroll; ++u) r[u] = T.template find<PV>(k[u]);   // -1 (past the end): a miss
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const bool hit = r[u] >= 0;
