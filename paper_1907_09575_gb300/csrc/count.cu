@@ -91,6 +91,15 @@ struct TaskWindow {
     int64_t shift;
 };
 
+// *p += 1 in shared memory when h is set: one predicated reduction, no
+// branch around it.  p must point into shared memory; when h is 0 the
+// address is formed but never accessed, so it may lie outside the array.
+__device__ __forceinline__ void add_if(unsigned* p, unsigned h) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\t@q red.shared.add.u32 [%0], 1;\n\t}"
+                 ::"r"(a), "r"(h) : "memory");
+}
+
 // bits [lo, hi) of a 32-bit mask, 0 <= lo <= hi <= 32
 __device__ __forceinline__ unsigned bit_range(int lo, int hi) {
     const unsigned up = (hi >= 32) ? 0xffffffffu : ((1u << hi) - 1u);
@@ -140,12 +149,12 @@ struct BitTab {
     __device__ __forceinline__ void probe_credit(int k, unsigned* cnt, unsigned& mine) const {
         const unsigned d = offset(k);
         const unsigned w = bm[d >> 5];
-        const unsigned b = d & 31;
-        const unsigned h = (w >> b) & 1u;
-        mine += h;
-        // popc of the bits up to and including b counts the hit itself
-        const int r1 = (int)pre[d >> 5] + __popc(w << (b ^ 31u));
-        if (h) atomicAdd(&cnt[r1 - 1], 1u);
+        // bit d & 31 moved to the top: the sign is the hit, and the popc
+        // counts the bits up to and including it
+        const unsigned x = w << (~d & 31u);
+        mine += x >> 31;
+        const int r1 = (int)pre[d >> 5] + __popc(x);
+        add_if(&cnt[r1 - 1], x >> 31);
     }
     // hit counters by rank (rank < slice <= 4096): one word each, so hits on
     // neighbouring entries never share an atomic's word
