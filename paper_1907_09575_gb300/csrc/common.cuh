@@ -129,6 +129,9 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t count, int64_t*
                         Alloc& al, cudaStream_t st);
 void exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t count,
                                int64_t* total_dev, Alloc& al, cudaStream_t st);
+// two int32 arrays of the same length (one launch when they are short)
+void exclusive_scan2_i32_to_i64(const int32_t* in0, int64_t* out0, int64_t* total0, const int32_t* in1,
+                                int64_t* out1, int64_t* total1, int64_t count, Alloc& al, cudaStream_t st);
 
 // Stable LSD radix sort of 64-bit keys on bits [lo, hi).  Sorted keys end up
 // in *keys (the two buffers may be swapped).  count <= 2^31 - 1.  With

@@ -952,8 +952,8 @@ void plan_units(UnitPlan& P, const GraphView* views_dev, const int64_t* vpre_dev
                                                            P.cl.get());
     }
     TC_LAUNCH_CHECK();
-    exclusive_scan_i32_to_i64(P.cs.get(), P.ps.get(), V, P.ps.get() + V, al, st);
-    exclusive_scan_i32_to_i64(P.cl.get(), P.pl.get(), V, P.pl.get() + V, al, st);
+    exclusive_scan2_i32_to_i64(P.cs.get(), P.ps.get(), P.ps.get() + V, P.cl.get(), P.pl.get(), P.pl.get() + V, V,
+                               al, st);
 }
 
 UnitLists fill_units(UnitPlan& P, int64_t ns, int64_t nl, Alloc& al, cudaStream_t st) {

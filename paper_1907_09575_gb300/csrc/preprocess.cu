@@ -281,6 +281,173 @@ __global__ void k_adj_rows(const uint64_t* __restrict__ keys, int64_t m, int bit
     }
 }
 
+// a5 by counting, for graphs small enough that no row of U can pass
+// kRowSortMax entries (in degree order a row of d entries has d neighbours
+// of degree >= d, so d^2 <= 2m): the oriented pairs are counted per row,
+// scattered into their row's slots, and each row is sorted where it lies.
+#ifndef TC_ORIENT_COUNT_MAX
+#define TC_ORIENT_COUNT_MAX (1ll << 24)
+#endif
+constexpr int64_t kOrientCountMaxM = TC_ORIENT_COUNT_MAX;
+constexpr int kRowSortMax = 8192;   // sqrt(2 * 2^25)
+static_assert(kOrientCountMaxM <= (int64_t)kRowSortMax * kRowSortMax / 2, "rows fit the row sort");
+constexpr int kRowSortThreads = 256;
+
+__global__ void k_orient_count(const uint64_t* __restrict__ E, int64_t m, int bits,
+                               const int32_t* __restrict__ perm, uint64_t* __restrict__ keys,
+                               int32_t* __restrict__ dplus) {
+    const uint64_t mask = (1ull << bits) - 1ull;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = E[e];
+        const uint32_t u = (uint32_t)perm[k >> bits], v = (uint32_t)perm[k & mask];
+        const uint64_t lo = min(u, v), hi = max(u, v);
+        keys[e] = (lo << bits) | hi;
+        atomicAdd(&dplus[lo], 1);
+    }
+}
+
+// out[off[u] + (u's arrival order)] = the pair; cur counts arrivals per row
+__global__ void k_orient_scatter(const uint64_t* __restrict__ keys, int64_t m, int bits,
+                                 const int64_t* __restrict__ off, int32_t* __restrict__ cur,
+                                 uint64_t* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = keys[e];
+        const int64_t u = (int64_t)(k >> bits);
+        out[off[u] + atomicAdd(&cur[u], 1)] = k;
+    }
+}
+
+// Bitonic sort of a warp's 32*E columns, lane l holding entries l*E ..
+// l*E + E - 1: exchanges at distances below E stay in a lane's registers,
+// longer ones pair lanes by a shuffle.
+template <int E>
+__device__ __forceinline__ void warp_bitonic(uint32_t (&x)[E]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 2; k <= 32 * E; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j < E) {
+#pragma unroll
+                for (int r = 0; r < E; ++r)
+                    if ((r & j) == 0) {
+                        const bool up = ((lane * E + r) & k) == 0;
+                        const uint32_t a = x[r], c = x[r | j];
+                        x[r] = up ? min(a, c) : max(a, c);
+                        x[r | j] = up ? max(a, c) : min(a, c);
+                    }
+            } else {
+                const int lj = j / E;
+                const bool low = (lane & lj) == 0;
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const uint32_t y = __shfl_xor_sync(0xffffffffu, x[r], lj);
+                    const bool up = ((lane * E + r) & k) == 0;
+                    x[r] = (low == up) ? min(x[r], y) : max(x[r], y);
+                }
+            }
+        }
+}
+
+template <int E>
+__device__ __forceinline__ void warp_sort_row(uint64_t* __restrict__ keys, int32_t* __restrict__ adj,
+                                              int64_t rb, int d, uint64_t row, uint64_t mask) {
+    const int lane = threadIdx.x & 31;
+    uint32_t x[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int q = lane * E + r;
+        x[r] = q < d ? (uint32_t)(keys[rb + q] & mask) : 0xffffffffu;
+    }
+    warp_bitonic<E>(x);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int q = lane * E + r;
+        if (q < d) {
+            keys[rb + q] = row | x[r];
+            adj[rb + q] = (int32_t)x[r];
+        }
+    }
+}
+
+// Rows of at most kWarpRowMax entries: one warp each, sorted in registers.
+// Longer rows are listed for k_row_sort_long.  adj = the columns.
+constexpr int kWarpRowMax = 256;
+__global__ void k_row_sort_short(uint64_t* __restrict__ keys, const int64_t* __restrict__ off, int64_t n,
+                                 int bits, int32_t* __restrict__ adj, int32_t* __restrict__ longrows,
+                                 int* __restrict__ nlong) {
+    const uint64_t mask = (1ull << bits) - 1ull;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+        const int64_t rb = off[r];
+        const int64_t d = off[r + 1] - rb;
+        const uint64_t row = (uint64_t)r << bits;
+        if (d > kWarpRowMax) {
+            if (lane == 0) longrows[atomicAdd(nlong, 1)] = (int32_t)r;
+        } else if (d > 128) {
+            warp_sort_row<kWarpRowMax / 32>(keys, adj, rb, (int)d, row, mask);
+        } else if (d > 64) {
+            warp_sort_row<4>(keys, adj, rb, (int)d, row, mask);
+        } else if (d > 32) {
+            warp_sort_row<2>(keys, adj, rb, (int)d, row, mask);
+        } else if (d > 1) {
+            warp_sort_row<1>(keys, adj, rb, (int)d, row, mask);
+        } else if (d == 1 && lane == 0) {
+            adj[rb] = (int32_t)(keys[rb] & mask);
+        }
+    }
+}
+
+// Rows of kWarpRowMax+1 .. kRowSortMax entries: one block each, a bitonic
+// sort of the columns in shared memory (a row's keys share their row bits).
+// A longer row (impossible within kOrientCountMaxM) sets error bit 8 and is
+// skipped.
+__global__ void __launch_bounds__(kRowSortThreads) k_row_sort_long(
+        uint64_t* __restrict__ keys, const int64_t* __restrict__ off, int bits, int32_t* __restrict__ adj,
+        const int32_t* __restrict__ longrows, const int* __restrict__ nlong, int* __restrict__ err) {
+    __shared__ uint32_t v[kRowSortMax];
+    const uint64_t mask = (1ull << bits) - 1ull;
+    const int nl = *nlong;
+    for (int x = blockIdx.x; x < nl; x += gridDim.x) {
+        const int64_t r = longrows[x];
+        const int64_t rb = off[r];
+        const int d = (int)(off[r + 1] - rb);
+        if (d > kRowSortMax) {
+            if (threadIdx.x == 0) atomicOr(err, 8);
+            continue;
+        }
+        int P = 2 * kWarpRowMax;
+        while (P < d) P <<= 1;
+        for (int q = threadIdx.x; q < P; q += blockDim.x)
+            v[q] = q < d ? (uint32_t)(keys[rb + q] & mask) : 0xffffffffu;
+        __syncthreads();
+        for (int k = 2; k <= P; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int q = threadIdx.x; q < P; q += blockDim.x) {
+                    const int l = q ^ j;
+                    if (l > q) {
+                        const uint32_t a = v[q], b = v[l];
+                        const bool up = (q & k) == 0;
+                        if ((a > b) == up) {
+                            v[q] = b;
+                            v[l] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        const uint64_t row = (uint64_t)r << bits;
+        for (int q = threadIdx.x; q < d; q += blockDim.x) {
+            keys[rb + q] = row | v[q];
+            adj[rb + q] = (int32_t)v[q];
+        }
+        __syncthreads();   // v is rewritten by the next row
+    }
+}
+
 template <class OffT>
 __global__ void k_store_offsets(const int64_t* __restrict__ off64, int64_t count,
                                 OffT* __restrict__ out) {
@@ -754,22 +921,52 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
         ab = Buf<uint64_t>(al, (size_t)std::max<int64_t>(m, 1));
         alt = ab.get();
     }
-    if (m > 0) {
+    if (m > 0 && m <= kOrientCountMaxM) {
         {
-            Prof prof_("k_orient", st);
-            k_orient<<<grid_for(m, kT, G), kT, 0, st>>>(keys, m, bits, g->perm, alt);
+            Prof prof_("k_orient_count", st);
+            k_orient_count<<<grid_for(m, kT, G), kT, 0, st>>>(keys, m, bits, g->perm, alt, dplus.get());
         }
         TC_LAUNCH_CHECK();
-        std::swap(keys, alt);
-        radix_sort_u64(&keys, &alt, m, 0, 2 * bits, al, st, scal.get());
+        // off = exclusive scan of dplus, with off[n] = m
+        exclusive_scan_i32_to_i64(dplus.get(), off64.get(), n, off64.get() + n, al, st);
+        TC_CUDA(cudaMemsetAsync(dplus.get(), 0, sizeof(int32_t) * (size_t)n, st));
         {
-            Prof prof_("k_adj_rows", st);
-            k_adj_rows<<<grid_for(m, kT, G), kT, 0, st>>>(keys, m, bits, g->adj, dplus.get());
+            Prof prof_("k_orient_scatter", st);
+            k_orient_scatter<<<grid_for(m, kT, G), kT, 0, st>>>(alt, m, bits, off64.get(), dplus.get(), keys);
         }
         TC_LAUNCH_CHECK();
+        Buf<int32_t> longrows(al, (size_t)(m / (kWarpRowMax + 1) + 1));
+        {
+            Prof prof_("k_row_sort_short", st);
+            k_row_sort_short<<<grid_for(32 * n, kT, G), kT, 0, st>>>(keys, off64.get(), n, bits, g->adj,
+                                                                    longrows.get(), scal.get() + 4);
+        }
+        TC_LAUNCH_CHECK();
+        {
+            Prof prof_("k_row_sort_long", st);
+            k_row_sort_long<<<(unsigned)std::min<int64_t>(m / (kWarpRowMax + 1) + 1, 4 * (int64_t)num_sms()),
+                              kRowSortThreads, 0, st>>>(keys, off64.get(), bits, g->adj, longrows.get(),
+                                                        scal.get() + 4, scal.get());
+        }
+        TC_LAUNCH_CHECK();
+    } else {
+        if (m > 0) {
+            {
+                Prof prof_("k_orient", st);
+                k_orient<<<grid_for(m, kT, G), kT, 0, st>>>(keys, m, bits, g->perm, alt);
+            }
+            TC_LAUNCH_CHECK();
+            std::swap(keys, alt);
+            radix_sort_u64(&keys, &alt, m, 0, 2 * bits, al, st, scal.get());
+            {
+                Prof prof_("k_adj_rows", st);
+                k_adj_rows<<<grid_for(m, kT, G), kT, 0, st>>>(keys, m, bits, g->adj, dplus.get());
+            }
+            TC_LAUNCH_CHECK();
+        }
+        // off = exclusive scan of dplus, with off[n] = m
+        exclusive_scan_i32_to_i64(dplus.get(), off64.get(), n, off64.get() + n, al, st);
     }
-    // off = exclusive scan of dplus, with off[n] = m
-    exclusive_scan_i32_to_i64(dplus.get(), off64.get(), n, off64.get() + n, al, st);
     if (g->off64) {
         TC_CUDA(cudaMemcpyAsync(g->off, off64.get(), 8 * (size_t)(n + 1), cudaMemcpyDeviceToDevice, st));
     } else {
@@ -880,6 +1077,7 @@ void preprocess_with_components(tc_graph* g, const int32_t* src_in, const int32_
     TC_CUDA(cudaMemcpyAsync(&nl, plan.pl.get() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     TC_CUDA(cudaStreamSynchronize(st));
     if (herr & 4) TC_FAIL(TC_ETIMEOUT, "tc_preprocess: a sort look-back wait ran past its bound");
+    if (herr & 8) TC_FAIL(TC_EUNSUPPORTED, "tc_preprocess: a row of U exceeds the row sort's bound");
     g->n_tasks = ntasks;
     g->stats.max_outdeg = maxout;
     g->stats.tasks = ntasks;

@@ -94,56 +94,62 @@ __global__ void __launch_bounds__(kThreads) k_tile_scan(const Tin* in, int64_t* 
         *total = run;  // the last thread's running sum after its items = grand total
 }
 
-// Arrays of up to kBlockMax entries in one launch: one block streams the
-// array through shared memory in chunks of kChunk entries (coalesced loads
-// and stores; each thread scans kPer contiguous entries of the chunk), the
-// running total carried from chunk to chunk.
+// Arrays of up to kBlockMax entries in one launch.  Warp w owns the
+// contiguous segment [w * 32 * per, (w + 1) * 32 * per), read a row of 32
+// entries at a time (lane l takes entry l of each row: coalesced).  Pass 1
+// sums each warp's segment; the warp sums are scanned across the block;
+// pass 2 re-reads the rows (now from cache) and scans each across the warp,
+// carrying the running sum from row to row.  in may equal out: each entry is
+// read by the lane that writes it, before it writes it.
 constexpr int kBlockThreads = 1024;
-constexpr int kPer = 4;
-constexpr int kChunk = kBlockThreads * kPer;
-constexpr int64_t kBlockMax = 16ll * kChunk;
+constexpr int64_t kBlockMax = 65536;
+constexpr int kRowBatch = 8;
 
+// Block b scans array b: two arrays of the same length in one launch.
 template <class Tin>
 __global__ void __launch_bounds__(kBlockThreads) k_block_scan(const Tin* in, int64_t* out, int64_t count,
-                                                              int64_t* total) {
-    __shared__ int64_t buf[kChunk];
+                                                              int64_t* total, const Tin* in1, int64_t* out1,
+                                                              int64_t* total1) {
+    if (blockIdx.x == 1) {
+        in = in1;
+        out = out1;
+        total = total1;
+    }
     __shared__ int64_t warp_sums[kBlockThreads / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int64_t carry = 0;
-    for (int64_t c0 = 0; c0 < count; c0 += kChunk) {
+    const int64_t per = (count + kBlockThreads - 1) / kBlockThreads;   // rows per warp
+    const int64_t seg = (int64_t)w * 32 * per;
+    int64_t sum = 0;
+    for (int64_t r0 = 0; r0 < per; r0 += kRowBatch) {
 #pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            const int idx = k * kBlockThreads + threadIdx.x;
-            buf[idx] = (c0 + idx < count) ? (int64_t)in[c0 + idx] : 0;
+        for (int u = 0; u < kRowBatch; ++u) {
+            const int64_t q = seg + (r0 + u) * 32 + lane;
+            sum += (r0 + u < per && q < count) ? (int64_t)in[q] : 0;
         }
-        __syncthreads();
-        int64_t v[kPer], sum = 0;
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            v[k] = buf[threadIdx.x * kPer + k];
-            sum += v[k];
-        }
-        const int64_t inc = warp_incl_scan(sum);
-        if (lane == 31) warp_sums[w] = inc;
-        __syncthreads();
-        if (w == 0) warp_sums[lane] = warp_incl_scan(warp_sums[lane]);
-        __syncthreads();
-        int64_t run = carry + (w > 0 ? warp_sums[w - 1] : 0) + inc - sum;
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            buf[threadIdx.x * kPer + k] = run;
-            run += v[k];
-        }
-        carry += warp_sums[kBlockThreads / 32 - 1];
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            const int idx = k * kBlockThreads + threadIdx.x;
-            if (c0 + idx < count) out[c0 + idx] = buf[idx];
-        }
-        __syncthreads();   // buf and warp_sums are rewritten by the next chunk
     }
-    if (total && threadIdx.x == 0) *total = carry;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) warp_sums[w] = sum;
+    __syncthreads();
+    if (w == 0) warp_sums[lane] = warp_incl_scan(warp_sums[lane]);
+    __syncthreads();
+    int64_t carry = (w > 0) ? warp_sums[w - 1] : 0;
+    for (int64_t r0 = 0; r0 < per; r0 += kRowBatch) {
+        int64_t v[kRowBatch];
+#pragma unroll
+        for (int u = 0; u < kRowBatch; ++u) {
+            const int64_t q = seg + (r0 + u) * 32 + lane;
+            v[u] = (r0 + u < per && q < count) ? (int64_t)in[q] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kRowBatch; ++u) {
+            const int64_t q = seg + (r0 + u) * 32 + lane;
+            const int64_t inc = warp_incl_scan(v[u]);
+            if (r0 + u < per && q < count) out[q] = carry + inc - v[u];
+            carry += __shfl_sync(0xffffffffu, inc, 31);
+        }
+    }
+    if (total && threadIdx.x == 0) *total = warp_sums[kBlockThreads / 32 - 1];
 }
 
 template <class Tin>
@@ -157,7 +163,8 @@ void scan_impl(const Tin* in, int64_t* out, int64_t count, int64_t* total_dev, A
     if (tiles > 1 && count <= kBlockMax) {
         {
             Prof prof_("k_block_scan", st);
-            k_block_scan<Tin><<<1, kBlockThreads, 0, st>>>(in, out, count, total_dev);
+            k_block_scan<Tin><<<1, kBlockThreads, 0, st>>>(in, out, count, total_dev, nullptr, nullptr,
+                                                            nullptr);
         }
         TC_LAUNCH_CHECK();
         return;
@@ -194,6 +201,20 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t count, int64_t*
 void exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t count,
                                int64_t* total_dev, Alloc& al, cudaStream_t st) {
     scan_impl<int32_t>(in, out, count, total_dev, al, st);
+}
+
+void exclusive_scan2_i32_to_i64(const int32_t* in0, int64_t* out0, int64_t* total0, const int32_t* in1,
+                                int64_t* out1, int64_t* total1, int64_t count, Alloc& al, cudaStream_t st) {
+    if (count <= 0 || count > kBlockMax) {
+        scan_impl<int32_t>(in0, out0, count, total0, al, st);
+        scan_impl<int32_t>(in1, out1, count, total1, al, st);
+        return;
+    }
+    {
+        Prof prof_("k_block_scan", st);
+        k_block_scan<int32_t><<<2, kBlockThreads, 0, st>>>(in0, out0, count, total0, in1, out1, total1);
+    }
+    TC_LAUNCH_CHECK();
 }
 
 }  // namespace tc
