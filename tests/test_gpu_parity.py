@@ -129,6 +129,23 @@ def test_wheels(tc, n):
         assert total == n - 1 and t[0] == n - 1 and np.all(t[1:n] == 2)
 
 
+def test_counting_csr_row_lengths(tc):
+    # a planted K_601 on random vertices among RMAT edges, in shuffled order:
+    # rows of U of every length up to 600 reach every sort of the counting
+    # CSR build (one, two, four or eight entries a lane; a block above 256)
+    rng = np.random.default_rng(11)
+    n = 4096
+    hs, hd = inputs.rmat(5, 12, 30000)
+    core = rng.choice(n, 601, replace=False).astype(np.int32)
+    iu, ju = np.triu_indices(601, 1)
+    src = np.concatenate([hs, core[iu]])
+    dst = np.concatenate([hd, core[ju]])
+    order = rng.permutation(src.size)
+    check(tc, src[order], dst[order], n)
+    _, _, st = gpu_count(tc, src[order], dst[order], n, per_vertex=False)
+    assert st["max_outdeg"] >= 600
+
+
 def test_bipartite_star_cycle(tc):
     rng = np.random.default_rng(0)
     e = [(x, 60 + y) for x in range(60) for y in range(50) if rng.random() < 0.4]
