@@ -8,11 +8,14 @@
 //
 // Tables (Section 5.2, "Modifying the hashing routine for sparser vertices"):
 // a bitmap over [min U_j, max U_j] when that label span fits (collision
-// free), else buckets of 4 slots with bucket = k AND (buckets - 1)
-// (tc_tuning.table_mode = 1 forces buckets everywhere).  A probe outside
-// [min U_j, max U_j] cannot hit -- the per-probe form of the early exit of
-// Section 5.2: a bitmap lookup clamps it onto a guard bit that is always
-// clear, a bucket lookup rejects it before reading the table.
+// free); else, for slices of at most kTagMaxEntries entries, a tag table
+// (one slot per label hash holding the rest of the hashed label and the
+// entry's rank: one load decides a probe exactly); else buckets of 4 slots
+// with bucket = k AND (buckets - 1) (tc_tuning.table_mode = 1 forces
+// buckets everywhere).  A probe outside [min U_j, max U_j] cannot hit --
+// the per-probe form of the early exit of Section 5.2: a bitmap lookup
+// clamps it onto a guard bit that is always clear, a bucket lookup rejects
+// it before reading the table, a tag lookup finds no equal tag.
 //
 // Work: units (graph, pivot, slice of U_j, range of tasks).  Pivots with
 // |U_j| <= 64 become warp units (a private table per warp); larger ones CTA
@@ -192,6 +195,77 @@ struct HashTab {
     }
 };
 
+#ifndef TC_TAG
+#define TC_TAG 1               // 0: buckets for every slice the bitmap cannot hold
+#endif
+#ifndef TC_TAG2_BIG
+#define TC_TAG2_BIG 1
+#endif
+#ifndef TC_TAG_MAX
+#define TC_TAG_MAX 2048
+#endif
+// Tag table, for slices of at most kTagMaxEntries entries whose labels are
+// too spread for the bitmap: p = k * kTagMul (mod 2^32) is a bijection of
+// the label; its top 12 bits pick one of 4096 slots and the slot keeps the
+// low 20 bits of p (the tag) with the entry's rank in bits 20..30, so one
+// 32-bit load decides membership exactly and gives the rank.  A slot two
+// entries map to holds kTagMulti; those entries go to a second table of
+// 2048 slots (another multiplier, 21-bit tags), and an entry that collides
+// there too is found by a binary search of the sorted slice.
+constexpr int kTagMaxEntries = TC_TAG_MAX;
+constexpr int kTagSlots = 4096, kTagSlots2 = TC_TAG2_BIG ? 4096 : 2048;
+constexpr int kTag2Shift = TC_TAG2_BIG ? 20 : 21;                 // tag bits of the second table
+constexpr unsigned kTag2Mask = (1u << kTag2Shift) - 1u;
+static_assert(kTagMaxEntries <= (1 << (31 - kTag2Shift)), "ranks fit both tables below bit 31");
+static_assert(kTagSlots + kTagSlots2 <= kRegionWords, "both tables fit the region");
+constexpr unsigned kTagMul = 0x9E3779B1u, kTagMul2 = 0x85EBCA77u;
+constexpr unsigned kTagEmpty = 0xffffffffu, kTagMulti = 0xfffffffeu;
+
+struct TagTab {
+    const unsigned* t1;        // kTagSlots words, then kTagSlots2 words
+    const int32_t* row;        // the sorted slice in device memory
+    int dp;
+    __device__ int slow(int k) const {
+        const unsigned p = (unsigned)k * kTagMul2;
+        const unsigned w = t1[kTagSlots + (p >> kTag2Shift)];
+        if (w != kTagMulti) return ((w & (0x80000000u | kTag2Mask)) == (p & kTag2Mask)) ? (int)(w >> kTag2Shift) : -1;
+        int a = 0, b = dp;
+        while (a < b) {
+            const int c = (a + b) >> 1;
+            if (__ldg(row + c) < k) a = c + 1; else b = c;
+        }
+        return (a < dp && __ldg(row + a) == k) ? a : -1;
+    }
+    template <bool PV>
+    __device__ __forceinline__ int find(int k) const {
+        const unsigned p = (unsigned)k * kTagMul;
+        const unsigned w = t1[p >> 20];
+        if (w == kTagMulti) return slow(k);
+        return ((w & 0x800fffffu) == (p & 0xfffffu)) ? (int)(w >> 20) : -1;
+    }
+    __device__ __forceinline__ unsigned bit(int k) const { return find<false>(k) >= 0; }
+    __device__ __forceinline__ void probe_credit(int k, unsigned* cnt, unsigned& mine) const {
+        const unsigned p = (unsigned)k * kTagMul;
+        const unsigned w = t1[p >> 20];
+        unsigned h = (w & 0x800fffffu) == (p & 0xfffffu);
+        int r = (int)(w >> 20);
+        if (w == kTagMulti) {
+            r = slow(k);
+            h = r >= 0;
+        }
+        mine += h;
+        add_if(&cnt[r], h);
+    }
+    __device__ __forceinline__ void credit(unsigned* cnt, int r) const { atomicAdd(&cnt[r], 1u); }
+    __device__ __forceinline__ unsigned credited(const unsigned* cnt, int r) const { return cnt[r]; }
+};
+
+__device__ __forceinline__ void tag_insert2(unsigned* t1, int k, int q) {
+    const unsigned p = (unsigned)k * kTagMul2;
+    unsigned* s = t1 + kTagSlots + (p >> kTag2Shift);
+    if (atomicCAS(s, kTagEmpty, ((unsigned)q << kTag2Shift) | (p & kTag2Mask)) != kTagEmpty) atomicExch(s, kTagMulti);
+}
+
 // Search (the list-based joint traversal of Section 3.1, lane-parallel): the
 // sorted pivot row U_j (at most 64 entries) sits in shared memory and each
 // lane places its probe in it by a branchless binary search.  No table is
@@ -256,7 +330,8 @@ __device__ __forceinline__ void probe_one(const Tab& T, int k, unsigned* cnt, un
 }
 
 // ---------------------------------------------------------------------------
-// One warp walks one long tail (>= 32 entries) adj[st, st+L): lane q of a
+// One warp walks one long tail (>= 32 entries with per-vertex counts, >= 64
+// for totals only) adj[st, st+L): lane q of a
 // step reads entry q, kUnroll steps a round.  Returns the task's hits (the
 // same in all lanes) with per-vertex counts, else 0.
 //
@@ -325,7 +400,7 @@ __device__ __forceinline__ void credit_task(unsigned long long* tnew, unsigned* 
 // ---------------------------------------------------------------------------
 // One warp takes up to 32 tasks [tb, min(tb+32, t1)).
 //
-// Long tails (>= 32 entries) are either walked right away (defer == null) or
+// Long tails (>= kShort entries) are either walked right away (defer == null) or
 // appended to the CTA's queue of long tasks (their index relative to t0), to
 // be shared out one task per warp later.  Short tails are concatenated: lane
 // q of a step reads entry q of the concatenation; its owner is the number of
@@ -366,7 +441,12 @@ __device__ __forceinline__ void warp_probe_group(const Task* __restrict__ tasks,
     const unsigned le = (2u << lane) - 1u;   // bits 0..lane
 
     // long tails
-    const bool lg = valid && len >= 32;
+    // tails shorter than kShort are concatenated across the lanes: 32 with
+    // per-vertex counts (a short task then spans at most two steps), 64
+    // for totals only (measured: the per-vertex short path costs more per
+    // step than the longer walk of tails of 32-63 entries)
+    constexpr int kShort = PV ? 32 : 64;
+    const bool lg = valid && len >= kShort;
     unsigned longm = __ballot_sync(0xffffffffu, lg);
     if (defer) {
         if (longm) {
@@ -388,7 +468,7 @@ __device__ __forceinline__ void warp_probe_group(const Task* __restrict__ tasks,
     }
 
     // short tails, concatenated
-    const int slen = (valid && len < 32) ? len : 0;
+    const int slen = (valid && len < kShort) ? len : 0;
     const int incl = warp_incl_scan_i32(slen);
     const int excl = incl - slen;
     const int total = __shfl_sync(0xffffffffu, incl, 31);
@@ -711,6 +791,33 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
             __syncthreads();
         }
         const BitTab T{region, pre, lo, hi};
+        cta_probe_unit<PV, WIN>(G, U, T, cnt, s_ctl, s_base, s_long, tlow, uh, probes);
+        __syncthreads();
+        if (PV)
+            for (int r = threadIdx.x; r < dp; r += blockDim.x) {
+                const unsigned h = T.credited(cnt, r);
+                if (h) atomicAdd(&G.tnew[G.adj[rb + r]], (unsigned long long)h);
+            }
+    } else if (TC_TAG && !hash_only && dp <= kTagMaxEntries) {
+        for (int s = threadIdx.x; s < kTagSlots + kTagSlots2; s += blockDim.x) region[s] = kTagEmpty;
+        __syncthreads();
+        for (int q = threadIdx.x; q < dp; q += blockDim.x) {
+            const int k = G.adj[rb + q];
+            const unsigned p = (unsigned)k * kTagMul;
+            unsigned* slot = region + (p >> 20);
+            if (atomicCAS(slot, kTagEmpty, ((unsigned)q << 20) | (p & 0xfffffu)) != kTagEmpty) {
+                // a shared slot: this entry and the one displaced (if still
+                // there) move to the second table
+                const unsigned old = atomicExch(slot, kTagMulti);
+                tag_insert2(region, k, q);
+                if (old != kTagMulti) {
+                    const int q2 = (int)(old >> 20);
+                    tag_insert2(region, G.adj[rb + q2], q2);
+                }
+            }
+        }
+        __syncthreads();
+        const TagTab T{region, G.adj + rb, dp};
         cta_probe_unit<PV, WIN>(G, U, T, cnt, s_ctl, s_base, s_long, tlow, uh, probes);
         __syncthreads();
         if (PV)

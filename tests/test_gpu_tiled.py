@@ -57,7 +57,7 @@ def offloaded(tc, spec):
     hs, hd = spec.generate()
     g = tc.preprocess(torch.from_numpy(hs).cuda(), torch.from_numpy(hd).cuda(), spec.n, offsets=64)
     st = g.stats()
-    g.count()
+    st["in_hbm"] = g.count(per_vertex=True)
     st["count_probes"] = sum(g.count_stats()["probes"])
     arena = st["device_bytes"]
     g.offload()
@@ -73,6 +73,10 @@ def test_rmat_scale20_within_an_eighth_of_its_arena(tc):
     total, t, ts = g.count_tiled(budget, per_vertex=True, allocator=cap.struct)
     torch.cuda.synchronize()
     assert total == want and np.array_equal(t, want_t)
+    # the in-HBM count of the same graph (its pivots of wide label span take
+    # tag tables) equals the oracle too
+    hbm_total, hbm_t = st["in_hbm"]
+    assert hbm_total == want and np.array_equal(hbm_t.cpu().numpy().astype(np.uint64)[:spec.n], want_t)
     assert cap.refused == 0 and cap.peak <= budget and not cap.live
     assert ts["tiles"] > 4 and ts["row_blocks"] > 1
     assert ts["tile_tasks"] == st["tasks"] and ts["probes"] == st["count_probes"]
