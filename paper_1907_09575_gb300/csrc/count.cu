@@ -198,36 +198,34 @@ struct HashTab {
 #ifndef TC_TAG
 #define TC_TAG 1               // 0: buckets for every slice the bitmap cannot hold
 #endif
-#ifndef TC_TAG2_BIG
-#define TC_TAG2_BIG 1
-#endif
-#ifndef TC_TAG_MAX
-#define TC_TAG_MAX 2048
-#endif
 // Tag table, for slices of at most kTagMaxEntries entries whose labels are
 // too spread for the bitmap: p = k * kTagMul (mod 2^32) is a bijection of
-// the label; its top 12 bits pick one of 4096 slots and the slot keeps the
-// low 20 bits of p (the tag) with the entry's rank in bits 20..30, so one
-// 32-bit load decides membership exactly and gives the rank.  A slot two
-// entries map to holds kTagMulti; those entries go to a second table of
-// 2048 slots (another multiplier, 21-bit tags), and an entry that collides
-// there too is found by a binary search of the sorted slice.
-constexpr int kTagMaxEntries = TC_TAG_MAX;
-constexpr int kTagSlots = 4096, kTagSlots2 = TC_TAG2_BIG ? 4096 : 2048;
-constexpr int kTag2Shift = TC_TAG2_BIG ? 20 : 21;                 // tag bits of the second table
+// the label; its top 13 bits pick one of 8192 slots (the whole table region)
+// and the slot keeps the low 19 bits of p (the tag) with the entry's rank in
+// bits 19..30, so one 32-bit load decides membership exactly and gives the
+// rank.  A slot two entries map to holds kTagMulti; those entries go to a
+// second table of 2048 slots (another multiplier, 21-bit tags) beside the
+// hit counters, and an entry that collides there too is found by a binary
+// search of the sorted slice.
+constexpr int kTagMaxEntries = 1024;                 // ranks below 2^10 in the second table
+constexpr int kTagSlots = 8192, kTag1Shift = 19;     // first table: 13 index bits, 19 tag bits
+constexpr unsigned kTag1Mask = (1u << kTag1Shift) - 1u;
+constexpr int kTagSlots2 = 2048, kTag2Shift = 21;    // second table: 11 index bits, 21 tag bits
 constexpr unsigned kTag2Mask = (1u << kTag2Shift) - 1u;
 static_assert(kTagMaxEntries <= (1 << (31 - kTag2Shift)), "ranks fit both tables below bit 31");
-static_assert(kTagSlots + kTagSlots2 <= kRegionWords, "both tables fit the region");
+static_assert(kTagSlots <= kRegionWords, "the first table fills at most the region");
+static_assert(kTagMaxEntries + kTagSlots2 <= kRegionWords / 2, "counters and second table share the counters' space");
 constexpr unsigned kTagMul = 0x9E3779B1u, kTagMul2 = 0x85EBCA77u;
 constexpr unsigned kTagEmpty = 0xffffffffu, kTagMulti = 0xfffffffeu;
 
 struct TagTab {
-    const unsigned* t1;        // kTagSlots words, then kTagSlots2 words
+    const unsigned* t1;        // kTagSlots words
+    const unsigned* t2;        // kTagSlots2 words
     const int32_t* row;        // the sorted slice in device memory
     int dp;
     __device__ int slow(int k) const {
         const unsigned p = (unsigned)k * kTagMul2;
-        const unsigned w = t1[kTagSlots + (p >> kTag2Shift)];
+        const unsigned w = t2[p >> kTag2Shift];
         if (w != kTagMulti) return ((w & (0x80000000u | kTag2Mask)) == (p & kTag2Mask)) ? (int)(w >> kTag2Shift) : -1;
         int a = 0, b = dp;
         while (a < b) {
@@ -239,16 +237,16 @@ struct TagTab {
     template <bool PV>
     __device__ __forceinline__ int find(int k) const {
         const unsigned p = (unsigned)k * kTagMul;
-        const unsigned w = t1[p >> 20];
+        const unsigned w = t1[p >> kTag1Shift];
         if (w == kTagMulti) return slow(k);
-        return ((w & 0x800fffffu) == (p & 0xfffffu)) ? (int)(w >> 20) : -1;
+        return ((w & (0x80000000u | kTag1Mask)) == (p & kTag1Mask)) ? (int)(w >> kTag1Shift) : -1;
     }
     __device__ __forceinline__ unsigned bit(int k) const { return find<false>(k) >= 0; }
     __device__ __forceinline__ void probe_credit(int k, unsigned* cnt, unsigned& mine) const {
         const unsigned p = (unsigned)k * kTagMul;
-        const unsigned w = t1[p >> 20];
-        unsigned h = (w & 0x800fffffu) == (p & 0xfffffu);
-        int r = (int)(w >> 20);
+        const unsigned w = t1[p >> kTag1Shift];
+        unsigned h = (w & (0x80000000u | kTag1Mask)) == (p & kTag1Mask);
+        int r = (int)(w >> kTag1Shift);
         if (w == kTagMulti) {
             r = slow(k);
             h = r >= 0;
@@ -260,9 +258,9 @@ struct TagTab {
     __device__ __forceinline__ unsigned credited(const unsigned* cnt, int r) const { return cnt[r]; }
 };
 
-__device__ __forceinline__ void tag_insert2(unsigned* t1, int k, int q) {
+__device__ __forceinline__ void tag_insert2(unsigned* t2, int k, int q) {
     const unsigned p = (unsigned)k * kTagMul2;
-    unsigned* s = t1 + kTagSlots + (p >> kTag2Shift);
+    unsigned* s = t2 + (p >> kTag2Shift);
     if (atomicCAS(s, kTagEmpty, ((unsigned)q << kTag2Shift) | (p & kTag2Mask)) != kTagEmpty) atomicExch(s, kTagMulti);
 }
 
@@ -799,25 +797,31 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
                 if (h) atomicAdd(&G.tnew[G.adj[rb + r]], (unsigned long long)h);
             }
     } else if (TC_TAG && !hash_only && dp <= kTagMaxEntries) {
-        for (int s = threadIdx.x; s < kTagSlots + kTagSlots2; s += blockDim.x) region[s] = kTagEmpty;
+        // the second table sits past the counters the slice can use (for
+        // totals only, where the counters are): a barrier first, as the
+        // counters were just cleared
+        unsigned* t2 = cnt + (PV ? kTagMaxEntries : 0);
+        __syncthreads();
+        for (int s = threadIdx.x; s < kTagSlots; s += blockDim.x) region[s] = kTagEmpty;
+        for (int s = threadIdx.x; s < kTagSlots2; s += blockDim.x) t2[s] = kTagEmpty;
         __syncthreads();
         for (int q = threadIdx.x; q < dp; q += blockDim.x) {
             const int k = G.adj[rb + q];
             const unsigned p = (unsigned)k * kTagMul;
-            unsigned* slot = region + (p >> 20);
-            if (atomicCAS(slot, kTagEmpty, ((unsigned)q << 20) | (p & 0xfffffu)) != kTagEmpty) {
+            unsigned* slot = region + (p >> kTag1Shift);
+            if (atomicCAS(slot, kTagEmpty, ((unsigned)q << kTag1Shift) | (p & kTag1Mask)) != kTagEmpty) {
                 // a shared slot: this entry and the one displaced (if still
                 // there) move to the second table
                 const unsigned old = atomicExch(slot, kTagMulti);
-                tag_insert2(region, k, q);
+                tag_insert2(t2, k, q);
                 if (old != kTagMulti) {
-                    const int q2 = (int)(old >> 20);
-                    tag_insert2(region, G.adj[rb + q2], q2);
+                    const int q2 = (int)(old >> kTag1Shift);
+                    tag_insert2(t2, G.adj[rb + q2], q2);
                 }
             }
         }
         __syncthreads();
-        const TagTab T{region, G.adj + rb, dp};
+        const TagTab T{region, t2, G.adj + rb, dp};
         cta_probe_unit<PV, WIN>(G, U, T, cnt, s_ctl, s_base, s_long, tlow, uh, probes);
         __syncthreads();
         if (PV)
@@ -863,7 +867,9 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
 //
 // Dynamic shared memory: per-warp bases (nw x 32 int64) | table region
 // (kRegionWords words; warp units use 192-word slices of it) | hit counters
-// (PV: kRegionWords/2 words) | long-task queue (unit_tasks x 16 bit).
+// (PV: kRegionWords/2 words, a tag table's second table past the first
+// kTagMaxEntries of them; totals only: the second table alone) | long-task
+// queue (unit_tasks x 16 bit).
 // ---------------------------------------------------------------------------
 template <bool PV, bool MERGE, bool WIN>
 __global__ void __launch_bounds__(256, TC_LARGE_MINB)
@@ -879,7 +885,8 @@ __global__ void __launch_bounds__(256, TC_LARGE_MINB)
     int64_t* s_base = reinterpret_cast<int64_t*>(smem) + 32 * w;
     unsigned* region = smem + 64 * nw;
     unsigned* cnt = region + kRegionWords;
-    unsigned short* s_long = reinterpret_cast<unsigned short*>(cnt + (PV ? kRegionWords / 2 : 0));
+    unsigned short* s_long =
+        reinterpret_cast<unsigned short*>(cnt + (PV ? kRegionWords / 2 : (TC_TAG ? kTagSlots2 : 0)));
     __shared__ unsigned long long s_work[6];   // units, tasks, staged for [warp, CTA] units
     if (threadIdx.x < 6) s_work[threadIdx.x] = 0;
     GraphAcc acc;
@@ -1114,7 +1121,7 @@ void adopt_units(tc_graph* g, const UnitLists& L, const tc_tuning& tt) {
 
 size_t count_smem_bytes(bool pv, int threads, int unit_tasks) {
     return sizeof(int64_t) * 32 * (size_t)(threads / 32) +
-           sizeof(unsigned) * (size_t)(kRegionWords + (pv ? kRegionWords / 2 : 0)) +
+           sizeof(unsigned) * (size_t)(kRegionWords + (pv ? kRegionWords / 2 : (TC_TAG ? kTagSlots2 : 0))) +
            sizeof(unsigned short) * (size_t)unit_tasks;
 }
 
