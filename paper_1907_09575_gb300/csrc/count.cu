@@ -195,9 +195,6 @@ struct HashTab {
     }
 };
 
-#ifndef TC_TAG
-#define TC_TAG 1               // 0: buckets for every slice the bitmap cannot hold
-#endif
 // Tag table, for slices of at most kTagMaxEntries entries whose labels are
 // too spread for the bitmap: p = k * kTagMul (mod 2^32) is a bijection of
 // the label; its top 13 bits pick one of 8192 slots (the whole table region)
@@ -215,6 +212,11 @@ constexpr unsigned kTag2Mask = (1u << kTag2Shift) - 1u;
 static_assert(kTagMaxEntries <= (1 << (31 - kTag2Shift)), "ranks fit both tables below bit 31");
 static_assert(kTagSlots <= kRegionWords, "the first table fills at most the region");
 static_assert(kTagMaxEntries + kTagSlots2 <= kRegionWords / 2, "counters and second table share the counters' space");
+#ifndef TC_TAG_SUB
+#define TC_TAG_SUB 1024        // entries of a tag table; a longer slice is probed in sub-slices
+#endif
+constexpr int kTagSub = TC_TAG_SUB;
+static_assert(kTagSub >= 1 && kTagSub <= kTagMaxEntries, "a sub-slice fits the tables");
 constexpr unsigned kTagMul = 0x9E3779B1u, kTagMul2 = 0x85EBCA77u;
 constexpr unsigned kTagEmpty = 0xffffffffu, kTagMulti = 0xfffffffeu;
 
@@ -743,18 +745,22 @@ __device__ __forceinline__ void cta_probe_unit(const GraphView& G, const Unit& U
     }
 }
 
-template <bool PV, bool WIN>
+// BUCKETS: the instance for tc_tuning.table_mode = 1, every slice in
+// 4-slot buckets; otherwise a bitmap when the slice's label span fits, else
+// tag tables.  The two are separate instances because the bucket code,
+// compiled into the default kernel, slowed its bitmap walk (2 %).
+template <bool PV, bool WIN, bool BUCKETS>
 __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int slice_max,
                                          unsigned* region, unsigned* cnt, int* s_ctl,
                                          int64_t* s_base, unsigned short* s_long,
                                          unsigned* s_wsum, unsigned long long* s_red,
-                                         bool hash_only, unsigned* tlow, uint64_t& hits, uint64_t& probes) {
+                                         unsigned* tlow, uint64_t& hits, uint64_t& probes) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int64_t rb = off_at(G, U.j) + (int64_t)U.slice * slice_max;
     const int64_t re = min64(off_at(G, U.j + 1), rb + slice_max);
     const int dp = (int)(re - rb);
     const int lo = G.adj[rb], hi = G.adj[re - 1];
-    const bool bitmap = !hash_only && (int64_t)hi - lo + 1 < 32ll * kBitWords;   // labels + guard bit
+    const bool bitmap = !BUCKETS && (int64_t)hi - lo + 1 < 32ll * kBitWords;   // labels + guard bit
     uint64_t uh = 0;
     if (PV)
         for (int s = threadIdx.x; s < kRegionWords / 2; s += blockDim.x) cnt[s] = 0;
@@ -796,39 +802,55 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
                 const unsigned h = T.credited(cnt, r);
                 if (h) atomicAdd(&G.tnew[G.adj[rb + r]], (unsigned long long)h);
             }
-    } else if (TC_TAG && !hash_only && dp <= kTagMaxEntries) {
-        // the second table sits past the counters the slice can use (for
-        // totals only, where the counters are): a barrier first, as the
-        // counters were just cleared
-        unsigned* t2 = cnt + (PV ? kTagMaxEntries : 0);
-        __syncthreads();
-        for (int s = threadIdx.x; s < kTagSlots; s += blockDim.x) region[s] = kTagEmpty;
-        for (int s = threadIdx.x; s < kTagSlots2; s += blockDim.x) t2[s] = kTagEmpty;
-        __syncthreads();
-        for (int q = threadIdx.x; q < dp; q += blockDim.x) {
-            const int k = G.adj[rb + q];
-            const unsigned p = (unsigned)k * kTagMul;
-            unsigned* slot = region + (p >> kTag1Shift);
-            if (atomicCAS(slot, kTagEmpty, ((unsigned)q << kTag1Shift) | (p & kTag1Mask)) != kTagEmpty) {
-                // a shared slot: this entry and the one displaced (if still
-                // there) move to the second table
-                const unsigned old = atomicExch(slot, kTagMulti);
-                tag_insert2(t2, k, q);
-                if (old != kTagMulti) {
-                    const int q2 = (int)(old >> kTag1Shift);
-                    tag_insert2(t2, G.adj[rb + q2], q2);
+    } else if (!BUCKETS) {
+        // tag tables over sub-slices of at most kTagMaxEntries entries, the
+        // unit's tasks probing each in turn (a slice that long and that
+        // spread is rare: none in RMAT scale 26)
+        for (int sb = 0; sb < dp; sb += kTagSub) {
+            const int sd = min(dp - sb, kTagSub);
+            const int64_t sr = rb + sb;
+            // the second table sits past the counters the slice can use (for
+            // totals only, where the counters are); a barrier first, as the
+            // counters were just cleared (or the last pass just read them)
+            unsigned* t2 = cnt + (PV ? kTagMaxEntries : 0);
+            __syncthreads();
+            if (sb > 0) {
+                if (threadIdx.x == 0) {
+                    s_ctl[0] = 0;
+                    s_ctl[1] = 0;
+                    s_ctl[2] = 0;
+                }
+                if (PV)
+                    for (int s = threadIdx.x; s < kTagMaxEntries; s += blockDim.x) cnt[s] = 0;
+            }
+            for (int s = threadIdx.x; s < kTagSlots; s += blockDim.x) region[s] = kTagEmpty;
+            for (int s = threadIdx.x; s < kTagSlots2; s += blockDim.x) t2[s] = kTagEmpty;
+            __syncthreads();
+            for (int q = threadIdx.x; q < sd; q += blockDim.x) {
+                const int k = G.adj[sr + q];
+                const unsigned p = (unsigned)k * kTagMul;
+                unsigned* slot = region + (p >> kTag1Shift);
+                if (atomicCAS(slot, kTagEmpty, ((unsigned)q << kTag1Shift) | (p & kTag1Mask)) != kTagEmpty) {
+                    // a shared slot: this entry and the one displaced (if still
+                    // there) move to the second table
+                    const unsigned old = atomicExch(slot, kTagMulti);
+                    tag_insert2(t2, k, q);
+                    if (old != kTagMulti) {
+                        const int q2 = (int)(old >> kTag1Shift);
+                        tag_insert2(t2, G.adj[sr + q2], q2);
+                    }
                 }
             }
+            __syncthreads();
+            const TagTab T{region, t2, G.adj + sr, sd};
+            cta_probe_unit<PV, WIN>(G, U, T, cnt, s_ctl, s_base, s_long, tlow, uh, probes);
+            __syncthreads();
+            if (PV)
+                for (int r = threadIdx.x; r < sd; r += blockDim.x) {
+                    const unsigned h = T.credited(cnt, r);
+                    if (h) atomicAdd(&G.tnew[G.adj[sr + r]], (unsigned long long)h);
+                }
         }
-        __syncthreads();
-        const TagTab T{region, t2, G.adj + rb, dp};
-        cta_probe_unit<PV, WIN>(G, U, T, cnt, s_ctl, s_base, s_long, tlow, uh, probes);
-        __syncthreads();
-        if (PV)
-            for (int r = threadIdx.x; r < dp; r += blockDim.x) {
-                const unsigned h = T.credited(cnt, r);
-                if (h) atomicAdd(&G.tnew[G.adj[rb + r]], (unsigned long long)h);
-            }
     } else {
         int* tab = reinterpret_cast<int*>(region);
         const unsigned buckets = hash_buckets(dp);
@@ -871,7 +893,7 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
 // kTagMaxEntries of them; totals only: the second table alone) | long-task
 // queue (unit_tasks x 16 bit).
 // ---------------------------------------------------------------------------
-template <bool PV, bool MERGE, bool WIN>
+template <bool PV, bool MERGE, bool WIN, bool BUCKETS>
 __global__ void __launch_bounds__(256, TC_LARGE_MINB)
     k_count(const GraphView* __restrict__ views, const Unit* __restrict__ large, int64_t nlarge,
             const Unit* __restrict__ small, int64_t nsmall, int slice_max, int table_mode,
@@ -886,7 +908,7 @@ __global__ void __launch_bounds__(256, TC_LARGE_MINB)
     unsigned* region = smem + 64 * nw;
     unsigned* cnt = region + kRegionWords;
     unsigned short* s_long =
-        reinterpret_cast<unsigned short*>(cnt + (PV ? kRegionWords / 2 : (TC_TAG ? kTagSlots2 : 0)));
+        reinterpret_cast<unsigned short*>(cnt + (PV ? kRegionWords / 2 : kTagSlots2));
     __shared__ unsigned long long s_work[6];   // units, tasks, staged for [warp, CTA] units
     if (threadIdx.x < 6) s_work[threadIdx.x] = 0;
     GraphAcc acc;
@@ -906,8 +928,8 @@ __global__ void __launch_bounds__(256, TC_LARGE_MINB)
         const Unit U = large[u];
         const GraphView G = views[U.g];
         acc.to(unit_target(G, U));
-        cta_unit<PV, WIN>(G, U, slice_max, region, cnt, s_ctl, s_base, s_long, s_wsum, s_red,
-                     table_mode == 1, tlow, acc.hits, probes);
+        cta_unit<PV, WIN, BUCKETS>(G, U, slice_max, region, cnt, s_ctl, s_base, s_long, s_wsum, s_red,
+                                   tlow, acc.hits, probes);
         if (threadIdx.x == 0) {
             s_work[1] += 1;
             s_work[3] += (unsigned long long)(U.t1 - U.t0);
@@ -933,7 +955,7 @@ __global__ void __launch_bounds__(256, TC_LARGE_MINB)
             const Unit U = small[u];
             const GraphView G = views[U.g];
             acc.to(unit_target(G, U));
-            warp_unit<PV, MERGE, WIN>(G, U, wregion, wcnt, s_base, table_mode == 1, merge_max, tlow, acc.hits,
+            warp_unit<PV, MERGE, WIN>(G, U, wregion, wcnt, s_base, BUCKETS, merge_max, tlow, acc.hits,
                                  probes, staged);
             if (lane == 0) {
                 atomicAdd(&s_work[0], 1ull);
@@ -1121,7 +1143,7 @@ void adopt_units(tc_graph* g, const UnitLists& L, const tc_tuning& tt) {
 
 size_t count_smem_bytes(bool pv, int threads, int unit_tasks) {
     return sizeof(int64_t) * 32 * (size_t)(threads / 32) +
-           sizeof(unsigned) * (size_t)(kRegionWords + (pv ? kRegionWords / 2 : (TC_TAG ? kTagSlots2 : 0))) +
+           sizeof(unsigned) * (size_t)(kRegionWords + (pv ? kRegionWords / 2 : kTagSlots2)) +
            sizeof(unsigned short) * (size_t)unit_tasks;
 }
 
@@ -1130,11 +1152,15 @@ using CountKernel = void (*)(const GraphView*, const Unit*, int64_t, const Unit*
 
 // the count kernel instance for a launch: per-vertex or totals, with or
 // without the search path for short pivot rows, or the instance that counts
-// one tile of a host-resident graph (a window of rows)
-CountKernel count_kernel(bool pv, bool merge, bool win) {
-    if (win) return pv ? k_count<true, false, true> : k_count<false, false, true>;
-    return pv ? (merge ? k_count<true, true, false> : k_count<true, false, false>)
-              : (merge ? k_count<false, true, false> : k_count<false, false, false>);
+// one tile of a host-resident graph (a window of rows); each in its bucket
+// form for table_mode 1 (the search path is not used there)
+CountKernel count_kernel(bool pv, bool merge, bool win, bool buckets) {
+    if (buckets)
+        return win ? (pv ? k_count<true, false, true, true> : k_count<false, false, true, true>)
+                   : (pv ? k_count<true, false, false, true> : k_count<false, false, false, true>);
+    if (win) return pv ? k_count<true, false, true, false> : k_count<false, false, true, false>;
+    return pv ? (merge ? k_count<true, true, false, false> : k_count<true, false, false, false>)
+              : (merge ? k_count<false, true, false, false> : k_count<false, false, false, false>);
 }
 
 CountLaunch prepare_count(const UnitLists& L, const tc_tuning& t, bool pv, bool win) {
@@ -1142,9 +1168,10 @@ CountLaunch prepare_count(const UnitLists& L, const tc_tuning& t, bool pv, bool 
     c.threads = t.cta_threads;
     c.smem = count_smem_bytes(pv, c.threads, t.cta_unit_tasks);
     c.pv = pv;
-    c.merge = t.merge_max_outdeg > 0 && !win;
+    c.buckets = t.table_mode == 1;
+    c.merge = t.merge_max_outdeg > 0 && !win && !c.buckets;
     c.win = win;
-    auto kern = count_kernel(pv, c.merge, c.win);
+    auto kern = count_kernel(pv, c.merge, c.win, c.buckets);
     TC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem));
     int per_sm = 0;
     TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, c.threads, c.smem));
@@ -1158,7 +1185,7 @@ CountLaunch prepare_count(const UnitLists& L, const tc_tuning& t, bool pv, bool 
 void launch_count_raw(const CountLaunch& c, const GraphView* views_dev, const UnitLists& L,
                       const tc_tuning& t, unsigned long long* ctr, cudaStream_t st, unsigned* tlow) {
     if (L.nlarge + L.nsmall == 0) return;
-    auto kern = count_kernel(c.pv, c.merge, c.win);
+    auto kern = count_kernel(c.pv, c.merge, c.win, c.buckets);
     kern<<<c.grid, c.threads, c.smem, st>>>(views_dev, L.large, L.nlarge, L.small, L.nsmall,
                                             t.slice_max, t.table_mode, t.merge_max_outdeg, tlow, ctr);
     TC_LAUNCH_CHECK();

@@ -72,6 +72,7 @@ struct CountLaunch {
     bool pv = false;
     bool merge = false;   // the instance with the search path for short pivot rows
     bool win = false;     // the instance that counts one tile (a window of rows)
+    bool buckets = false; // the instance that puts every CTA slice in 4-slot buckets (table_mode 1)
 };
 // Sets the kernel's shared-memory attribute and sizes the persistent grid
 // (not a stream operation: call it outside stream capture).
