@@ -197,16 +197,16 @@ struct HashTab {
 
 // Tag table, for slices of at most kTagMaxEntries entries whose labels are
 // too spread for the bitmap: p = k * kTagMul (mod 2^32) is a bijection of
-// the label; its top 13 bits pick one of 8192 slots (the whole table region)
-// and the slot keeps the low 19 bits of p (the tag) with the entry's rank in
-// bits 19..30, so one 32-bit load decides membership exactly and gives the
-// rank.  A slot two entries map to holds kTagMulti; those entries go to a
-// second table of 2048 slots (another multiplier, 21-bit tags) beside the
-// hit counters, and an entry that collides there too is found by a binary
-// search of the sorted slice.
+// the label; its top b bits pick one of 2^b slots (per-vertex: about 8 an
+// entry, 1024 to 8192; totals only: 8192, the whole table region) and the
+// slot keeps the low 32 - b bits of p (the tag) with the entry's rank in
+// the bits above, below bit 31, so one 32-bit load decides membership
+// exactly and gives the rank.  A slot two entries map to holds kTagMulti;
+// those entries go to a second table of 2048 slots (another multiplier,
+// 21-bit tags) beside the hit counters, and an entry that collides there
+// too is found by a binary search of the sorted slice.
 constexpr int kTagMaxEntries = 1024;                 // ranks below 2^10 in the second table
-constexpr int kTagSlots = 8192, kTag1Shift = 19;     // first table: 13 index bits, 19 tag bits
-constexpr unsigned kTag1Mask = (1u << kTag1Shift) - 1u;
+constexpr int kTagSlots = 8192;                      // first table: at most 13 index bits
 constexpr int kTagSlots2 = 2048, kTag2Shift = 21;    // second table: 11 index bits, 21 tag bits
 constexpr unsigned kTag2Mask = (1u << kTag2Shift) - 1u;
 static_assert(kTagMaxEntries <= (1 << (31 - kTag2Shift)), "ranks fit both tables below bit 31");
@@ -221,10 +221,12 @@ constexpr unsigned kTagMul = 0x9E3779B1u, kTagMul2 = 0x85EBCA77u;
 constexpr unsigned kTagEmpty = 0xffffffffu, kTagMulti = 0xfffffffeu;
 
 struct TagTab {
-    const unsigned* t1;        // kTagSlots words
+    const unsigned* t1;        // 2^(32 - s1) words
     const unsigned* t2;        // kTagSlots2 words
     const int32_t* row;        // the sorted slice in device memory
     int dp;
+    int s1;                    // tag bits of the first table
+    unsigned m1;               // (1 << s1) - 1
     __device__ int slow(int k) const {
         const unsigned p = (unsigned)k * kTagMul2;
         const unsigned w = t2[p >> kTag2Shift];
@@ -239,16 +241,16 @@ struct TagTab {
     template <bool PV>
     __device__ __forceinline__ int find(int k) const {
         const unsigned p = (unsigned)k * kTagMul;
-        const unsigned w = t1[p >> kTag1Shift];
+        const unsigned w = t1[p >> s1];
         if (w == kTagMulti) return slow(k);
-        return ((w & (0x80000000u | kTag1Mask)) == (p & kTag1Mask)) ? (int)(w >> kTag1Shift) : -1;
+        return ((w & (0x80000000u | m1)) == (p & m1)) ? (int)(w >> s1) : -1;
     }
     __device__ __forceinline__ unsigned bit(int k) const { return find<false>(k) >= 0; }
     __device__ __forceinline__ void probe_credit(int k, unsigned* cnt, unsigned& mine) const {
         const unsigned p = (unsigned)k * kTagMul;
-        const unsigned w = t1[p >> kTag1Shift];
-        unsigned h = (w & (0x80000000u | kTag1Mask)) == (p & kTag1Mask);
-        int r = (int)(w >> kTag1Shift);
+        const unsigned w = t1[p >> s1];
+        unsigned h = (w & (0x80000000u | m1)) == (p & m1);
+        int r = (int)(w >> s1);
         if (w == kTagMulti) {
             r = slow(k);
             h = r >= 0;
@@ -762,8 +764,10 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
     const int lo = G.adj[rb], hi = G.adj[re - 1];
     const bool bitmap = !BUCKETS && (int64_t)hi - lo + 1 < 32ll * kBitWords;   // labels + guard bit
     uint64_t uh = 0;
+    // counters: by rank (< dp) for bitmaps and tag tables, by 16-bit slot
+    // for buckets
     if (PV)
-        for (int s = threadIdx.x; s < kRegionWords / 2; s += blockDim.x) cnt[s] = 0;
+        for (int s = threadIdx.x; s < (BUCKETS ? kRegionWords / 2 : dp); s += blockDim.x) cnt[s] = 0;
     if (bitmap) {
         const int words = ((hi - lo + 1) >> 5) + 1;
         for (int s = threadIdx.x; s < words; s += blockDim.x) region[s] = 0;
@@ -823,26 +827,33 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
                 if (PV)
                     for (int s = threadIdx.x; s < kTagMaxEntries; s += blockDim.x) cnt[s] = 0;
             }
-            for (int s = threadIdx.x; s < kTagSlots; s += blockDim.x) region[s] = kTagEmpty;
+            // index bits: with per-vertex counts 2^b1 >= 8 * sd, 10..13 (the
+            // rank then fits below bit 31; less to clear a unit), for totals
+            // only 13 (fewer shared slots: measured faster each way)
+            int b1 = PV ? 10 : 13;
+            while (b1 < 13 && (1 << b1) < 8 * sd) ++b1;
+            const int s1 = 32 - b1;
+            const unsigned m1 = (1u << s1) - 1u;
+            for (int s = threadIdx.x; s < (1 << b1); s += blockDim.x) region[s] = kTagEmpty;
             for (int s = threadIdx.x; s < kTagSlots2; s += blockDim.x) t2[s] = kTagEmpty;
             __syncthreads();
             for (int q = threadIdx.x; q < sd; q += blockDim.x) {
                 const int k = G.adj[sr + q];
                 const unsigned p = (unsigned)k * kTagMul;
-                unsigned* slot = region + (p >> kTag1Shift);
-                if (atomicCAS(slot, kTagEmpty, ((unsigned)q << kTag1Shift) | (p & kTag1Mask)) != kTagEmpty) {
+                unsigned* slot = region + (p >> s1);
+                if (atomicCAS(slot, kTagEmpty, ((unsigned)q << s1) | (p & m1)) != kTagEmpty) {
                     // a shared slot: this entry and the one displaced (if still
                     // there) move to the second table
                     const unsigned old = atomicExch(slot, kTagMulti);
                     tag_insert2(t2, k, q);
                     if (old != kTagMulti) {
-                        const int q2 = (int)(old >> kTag1Shift);
+                        const int q2 = (int)(old >> s1);
                         tag_insert2(t2, G.adj[sr + q2], q2);
                     }
                 }
             }
             __syncthreads();
-            const TagTab T{region, t2, G.adj + sr, sd};
+            const TagTab T{region, t2, G.adj + sr, sd, s1, m1};
             cta_probe_unit<PV, WIN>(G, U, T, cnt, s_ctl, s_base, s_long, tlow, uh, probes);
             __syncthreads();
             if (PV)
