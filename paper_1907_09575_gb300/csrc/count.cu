@@ -755,9 +755,8 @@ template <bool PV, bool WIN, bool BUCKETS>
 __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int slice_max,
                                          unsigned* region, unsigned* cnt, int* s_ctl,
                                          int64_t* s_base, unsigned short* s_long,
-                                         unsigned* s_wsum, unsigned long long* s_red,
-                                         unsigned* tlow, uint64_t& hits, uint64_t& probes) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+                                         unsigned* s_wsum, unsigned* tlow, uint64_t& hits, uint64_t& probes) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t rb = off_at(G, U.j) + (int64_t)U.slice * slice_max;
     const int64_t re = min64(off_at(G, U.j + 1), rb + slice_max);
     const int dp = (int)(re - rb);
@@ -881,14 +880,9 @@ __device__ __forceinline__ void cta_unit(const GraphView& G, const Unit& U, int 
     }
     hits += uh;
     if (PV) {
+        // j's credit: each warp adds its share (no barrier at the unit's end)
         uh = warp_sum_u64(uh);
-        if (lane == 0) s_red[w] = uh;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long tot = 0;
-            for (int q = 0; q < nw; ++q) tot += s_red[q];
-            if (tot) atomicAdd(&G.tnew[G.jbase + U.j], tot);
-        }
+        if (lane == 0 && uh) atomicAdd(&G.tnew[G.jbase + U.j], (unsigned long long)uh);
     }
 }
 
@@ -912,7 +906,6 @@ __global__ void __launch_bounds__(256, TC_LARGE_MINB)
     extern __shared__ __align__(16) unsigned smem[];
     __shared__ long long s_unit;
     __shared__ int s_ctl[4];
-    __shared__ unsigned long long s_red[32];
     __shared__ unsigned s_wsum[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int64_t* s_base = reinterpret_cast<int64_t*>(smem) + 32 * w;
@@ -939,7 +932,7 @@ __global__ void __launch_bounds__(256, TC_LARGE_MINB)
         const Unit U = large[u];
         const GraphView G = views[U.g];
         acc.to(unit_target(G, U));
-        cta_unit<PV, WIN, BUCKETS>(G, U, slice_max, region, cnt, s_ctl, s_base, s_long, s_wsum, s_red,
+        cta_unit<PV, WIN, BUCKETS>(G, U, slice_max, region, cnt, s_ctl, s_base, s_long, s_wsum,
                                    tlow, acc.hits, probes);
         if (threadIdx.x == 0) {
             s_work[1] += 1;
