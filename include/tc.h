@@ -140,8 +140,13 @@ TC_API tc_status tc_preprocess(const int32_t* src, const int32_t* dst, int64_t n
  * tc_count -- Eq. 1 and Eq. 2 over the graph: the exact number of triangles,
  * and optionally the number of triangles through each vertex.
  *
- *   g            a graph from tc_preprocess (not modified; one count at a
- *                time per graph, since the work queues live in its arena).
+ *   g            a graph from tc_preprocess.  Its adjacency is not changed,
+ *                but the call updates what the graph caches for counting:
+ *                the work units (rebuilt when the tuning differs from the
+ *                last count's), the 32-bit per-task counters of per-vertex
+ *                counts, and the stream its allocations are ordered on.  So
+ *                one count at a time per graph; counts of different graphs
+ *                may run concurrently.
  *   tune         NULL for defaults.
  *   total_host   if non-NULL, receives the total; the call then synchronises
  *                the stream.
@@ -155,7 +160,7 @@ TC_API tc_status tc_preprocess(const int32_t* src, const int32_t* dst, int64_t n
  * Errors: TC_EINVAL for NULL g, or both totals NULL and per_vertex_dev NULL;
  * TC_ECUDA.
  */
-TC_API tc_status tc_count(const tc_graph* g, const tc_tuning* tune, uint64_t* total_host,
+TC_API tc_status tc_count(tc_graph* g, const tc_tuning* tune, uint64_t* total_host,
                    uint64_t* total_dev, uint64_t* per_vertex_dev, void* stream);
 
 /*
@@ -182,10 +187,11 @@ TC_API tc_status tc_preprocess_components(const int32_t* src, const int32_t* dst
 /*
  * tc_count_components -- Eq. 1 / Eq. 2 per component of a graph from
  * tc_preprocess_components: comp_totals_dev (device, num_comps uint64)
- * receives each component's triangle count.  Stream ordered.
+ * receives each component's triangle count.  Stream ordered.  Updates the
+ * graph's counting caches as tc_count does (one count at a time per graph).
  * Errors: TC_EINVAL for NULL arguments or a graph without components.
  */
-TC_API tc_status tc_count_components(const tc_graph* g, const tc_tuning* tune,
+TC_API tc_status tc_count_components(tc_graph* g, const tc_tuning* tune,
                                      uint64_t* comp_totals_dev, void* stream);
 
 /*

@@ -282,7 +282,7 @@ tc_status tc_preprocess_components(const int32_t* src, const int32_t* dst, int64
     TC_API_END
 }
 
-tc_status tc_count_components(const tc_graph* g, const tc_tuning* tune, uint64_t* comp_totals_dev,
+tc_status tc_count_components(tc_graph* g, const tc_tuning* tune, uint64_t* comp_totals_dev,
                               void* stream) {
     TC_API_BEGIN
     if (!g || !comp_totals_dev) TC_FAIL(TC_EINVAL, "tc_count_components: NULL argument");
@@ -292,12 +292,12 @@ tc_status tc_count_components(const tc_graph* g, const tc_tuning* tune, uint64_t
     tc_tuning t;
     tuning_resolve(tune, &t);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const_cast<tc_graph*>(g)->alloc.stream = st;
+    g->alloc.stream = st;
     count_components(g, t, comp_totals_dev, st);
     TC_API_END
 }
 
-tc_status tc_count(const tc_graph* g, const tc_tuning* tune, uint64_t* total_host,
+tc_status tc_count(tc_graph* g, const tc_tuning* tune, uint64_t* total_host,
                    uint64_t* total_dev, uint64_t* per_vertex_dev, void* stream) {
     TC_API_BEGIN
     if (!g) TC_FAIL(TC_EINVAL, "tc_count: graph is NULL");
@@ -307,7 +307,7 @@ tc_status tc_count(const tc_graph* g, const tc_tuning* tune, uint64_t* total_hos
     tc_tuning t;
     tuning_resolve(tune, &t);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const_cast<tc_graph*>(g)->alloc.stream = st;
+    g->alloc.stream = st;
     count(g, t, total_dev, per_vertex_dev, st);
     if (total_host) {
         unsigned long long v = 0;

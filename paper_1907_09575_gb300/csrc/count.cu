@@ -1217,9 +1217,8 @@ void build_units(tc_graph* g, const tc_tuning& t, cudaStream_t st) {
     adopt_units(g, L, tt);
 }
 
-void count_components(const tc_graph* gc, const tc_tuning& t, uint64_t* comp_totals_dev,
+void count_components(tc_graph* g, const tc_tuning& t, uint64_t* comp_totals_dev,
                       cudaStream_t st) {
-    tc_graph* g = const_cast<tc_graph*>(gc);
     const tc_tuning tt = clamp_tuning(size_tuning(t, g->m));
     if (!tuning_equal(tt, g->units_tuning)) build_units(g, tt, st);
     TC_CUDA(cudaMemsetAsync(g->counters, 0, sizeof(unsigned long long) * CTR_COUNT, st));
@@ -1234,9 +1233,9 @@ void count_components(const tc_graph* gc, const tc_tuning& t, uint64_t* comp_tot
                             cudaMemcpyDeviceToDevice, st));
 }
 
-void count(const tc_graph* gc, const tc_tuning& t, uint64_t* total_dev, uint64_t* per_vertex_dev,
+void count(tc_graph* g, const tc_tuning& t, uint64_t* total_dev, uint64_t* per_vertex_dev,
            cudaStream_t st) {
-    tc_graph* g = const_cast<tc_graph*>(gc);   // unit lists are a cache of the tuning
+    // the unit lists are a cache of the tuning they were built for
     const tc_tuning tt = clamp_tuning(size_tuning(t, g->m));
     if (!tuning_equal(tt, g->units_tuning)) build_units(g, tt, st);
     const bool pv = per_vertex_dev != nullptr;

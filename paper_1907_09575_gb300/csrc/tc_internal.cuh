@@ -88,10 +88,10 @@ void launch_count(const GraphView* views_dev, const UnitLists& L, const tc_tunin
                   unsigned long long* ctr, cudaStream_t st, bool profile, unsigned* tlow = nullptr,
                   bool win = false);
 void build_units(tc_graph* g, const tc_tuning& t, cudaStream_t st);
-void count(const tc_graph* g, const tc_tuning& t, uint64_t* total_dev, uint64_t* per_vertex_dev,
+void count(tc_graph* g, const tc_tuning& t, uint64_t* total_dev, uint64_t* per_vertex_dev,
            cudaStream_t st);
 // Per-component totals of a graph preprocessed with components.
-void count_components(const tc_graph* g, const tc_tuning& t, uint64_t* comp_totals_dev,
+void count_components(tc_graph* g, const tc_tuning& t, uint64_t* comp_totals_dev,
                       cudaStream_t st);
 // Marks the graph's vertices with components [vpre[c], vpre[c+1]) -> c and
 // checks that every pair stays inside one component (TC_EINVAL otherwise).
