@@ -84,8 +84,11 @@ typedef struct {
     int32_t cta_threads;       /* threads per CTA of the large-pivot kernel (64..256) */
     int32_t slice_max;         /* pivot entries tabled at once by one CTA (64..4096) */
     int32_t table_mode;        /* 0: a bitmap when the pivot's label span fits (the
-                                  direct-index case of Section 5.2), else a hash;
-                                  1: hash tables only (the hashed-pivot ablation) */
+                                  direct-index case of Section 5.2), else an exact
+                                  tag table (a hash that is a bijection of the
+                                  label); 1: the AND-hash of Section 5.2 in 4-slot
+                                  buckets for every pivot (the hashed-pivot
+                                  ablation; merge_max_outdeg is then not used) */
     int32_t merge_max_outdeg;  /* warp-unit pivots with |U_j| <= this build no table:
                                   each lane searches the sorted row (the list-based
                                   traversal of Section 3.1); 0 = never (<= 64) */
